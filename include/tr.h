@@ -1,0 +1,193 @@
+/*
+ * tr.h -- C ABI of libtr, a B300 (sm_103a) transform-reduce-scan library.
+ *
+ * The library evaluates a fixed family of "hdc" maps -- functions written once
+ * and callable from host code, device code and at compile time, the subject of
+ * Mejstrik, "__host__ __device__ -- Generic programming in Cuda" (Sec. 2.3
+ * "host device everything", Sec. 2.6 "Experimental relaxed constexpr" and the
+ * hdc helper of Sec. 4) -- over large device arrays:
+ *
+ *     y_i = f(x_i)                               tr_map
+ *     sum / min / max of f over the array        tr_reduce
+ *     the same per segment [off[s], off[s+1])    tr_segmented_reduce
+ *     inclusive prefix sums of f                 tr_scan
+ *
+ * Conventions (all entry points):
+ *   - Every pointer named d_* or documented "device" is CUDA device memory
+ *     owned by the caller; the library never frees it and never allocates
+ *     per call.  Host pointers (map coefficients) are read during the call
+ *     only.
+ *   - Work is enqueued asynchronously on exec->stream (a cudaStream_t; NULL is
+ *     the legacy default stream).  No call synchronises, except tr_check.
+ *   - Errors follow the paper's convention (Sec. 1.2.1 "Cuda error checking"):
+ *     a status code, 0 = success.  Argument errors are detected before any
+ *     launch and nothing is enqueued.  Errors found on the device are never
+ *     raised with a trap (the paper's release_assert of Sec. 2.4 calls
+ *     __trap(), which poisons the CUDA context); instead the kernel writes a
+ *     status word into the workspace and returns, and tr_check() reports it.
+ *   - The workspace is caller-owned device memory of at least the size the
+ *     matching *_workspace_size() call reports, 256-byte aligned and
+ *     zero-filled before its first use (tr_workspace_init, or cudaMemset to
+ *     0).  Every op leaves it ready for the next op; after an op reported an
+ *     error, re-initialise it.  Ops that may run concurrently need distinct
+ *     workspaces.
+ *   - n = 0 is valid everywhere: sums are 0, min is +inf (UINT32_MAX for u32),
+ *     max is -inf (0 for u32), scans and maps write nothing.
+ */
+#ifndef TR_H
+#define TR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tr_status {
+  TR_OK = 0,
+  TR_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad enum, overlap */
+  TR_ERR_ALIGNMENT = 2,     /* a pointer not aligned to its element size */
+  TR_ERR_UNSUPPORTED = 3,   /* (dtype, map, op) combination not provided */
+  TR_ERR_WORKSPACE = 4,     /* workspace missing or smaller than required */
+  TR_ERR_CUDA = 5,          /* a CUDA runtime call failed (see tr_last_error) */
+  TR_ERR_TIMEOUT = 6,       /* a bounded device-side wait ran out */
+  TR_ERR_DEVICE_ASSERT = 7  /* a device-side input check failed (e.g. offsets) */
+} tr_status;
+
+typedef enum tr_dtype {
+  TR_F16 = 0,
+  TR_BF16 = 1,
+  TR_F32 = 2,
+  TR_F64 = 3,
+  TR_U32 = 4,
+  TR_U64 = 5,
+  TR_NONE = 15
+} tr_dtype;
+
+/* The map family.  Float maps compute in FP32 for f16/bf16/f32 storage and in
+ * FP64 for f64 storage; the integer mixers take u32. */
+typedef enum tr_map_kind {
+  TR_MAP_IDENTITY = 0,    /* f(x) = x                                        */
+  TR_MAP_SQUARE = 1,      /* f(x) = x * x                                    */
+  TR_MAP_HORNER = 2,      /* p(x) = c_d; p = fma(p, x, c_k), k = d-1..0       */
+  TR_MAP_RATIONAL = 3,    /* P(x) / Q(x), each by Horner, one IEEE division   */
+  TR_MAP_NEWTON_CBRT = 4, /* y0 = sign(x); y <- (2y + x/(y*y))/3, iters times */
+  TR_MAP_XORSHIFT32 = 5,  /* x^=x<<13; x^=x>>17; x^=x<<5 (Marsaglia 2003)     */
+  TR_MAP_SPLITMIX32 = 6   /* z=x+0x9E3779B9; z=(z^z>>16)*0x6A09E667;
+                             z=(z^z>>13)*0xBB67AE85; z^=z>>16 (mod 2^32)      */
+} tr_map_kind;
+
+#define TR_MAX_DEGREE 31
+
+/* A map of the family.  coef_p / coef_q: host arrays of deg+1 FP64
+ * coefficients in ascending powers (c_0 first); copied at the call and rounded
+ * to FP32 for FP32-compute paths.  deg_p, deg_q in [0, TR_MAX_DEGREE]; unused
+ * fields are ignored.  iters in [0, 64] for TR_MAP_NEWTON_CBRT. */
+typedef struct tr_map_desc {
+  int32_t kind; /* tr_map_kind */
+  int32_t deg_p;
+  int32_t deg_q;
+  int32_t iters;
+  const double* coef_p;
+  const double* coef_q;
+} tr_map_desc;
+
+enum { TR_SUM = 1, TR_MIN = 2, TR_MAX = 4 };
+
+/* Execution context of one call. */
+typedef struct tr_exec {
+  void* stream;            /* cudaStream_t, NULL = legacy default stream */
+  void* workspace;         /* device memory, see conventions above */
+  size_t workspace_bytes;
+  uint32_t wait_timeout_us;  /* bound on each device-side wait; 0 = 1,000,000 */
+  int32_t reserved;
+  int64_t debug_stall_tile;  /* scan only, for fault tests: the tile with this
+                                id never publishes its prefix, so its
+                                successors' waits run out; -1 = off */
+} tr_exec;
+
+/* ---- status and workspace ------------------------------------------------ */
+
+/* Static text for a status code. */
+const char* tr_status_string(tr_status s);
+
+/* Text describing the last failing call on this host thread ("" if none). */
+const char* tr_last_error(void);
+
+/* Zero-fill a workspace (cudaMemsetAsync on stream). */
+tr_status tr_workspace_init(void* d_workspace, size_t bytes, void* stream);
+
+/* Synchronise exec->stream, then read and clear the device status word in
+ * exec->workspace.  Returns TR_ERR_CUDA if the stream reported an error,
+ * otherwise the first device-side error recorded since the last tr_check
+ * (TR_ERR_TIMEOUT, TR_ERR_DEVICE_ASSERT) or TR_OK. */
+tr_status tr_check(const tr_exec* exec);
+
+/* ---- map ------------------------------------------------------------------ */
+
+/* y_i = f(x_i), i < n.  xt: F16/BF16/F32 (FP32 compute), F64 (FP64 compute) or
+ * U32 (mixers and identity).  yt is the compute type: F32 for FP32 compute,
+ * F64 for F64, U32 for U32.  y may equal x when xt == yt; partial overlap is
+ * an error.  Needs no workspace (exec->workspace may be NULL).  Pointers must
+ * be aligned to their element size; 16-byte aligned x and y take the 128-bit
+ * vector path. */
+tr_status tr_map(const tr_map_desc* map, const void* d_x, tr_dtype xt, void* d_y, tr_dtype yt, int64_t n,
+                 const tr_exec* exec);
+
+/* ---- full reduction ------------------------------------------------------ */
+
+tr_status tr_reduce_workspace_size(int64_t n, tr_dtype xt, size_t* bytes);
+
+/* sum / min / max of f(x_i), i < n, selected by ops (TR_SUM|TR_MIN|TR_MAX).
+ * Results are written to DEVICE memory (one element each):
+ *   FP32 compute: per-thread compensated (Kahan) sums of pairwise vector sums,
+ *                 float-float warp/block combination, FP64 across blocks;
+ *                 sum_t F32 or F64; min/max F32.
+ *   FP64 compute: FP64 sums; sum_t F64; min/max F64.
+ *   U32 mixers:   exact sum_t U64 (or U32 modulo 2^32); min/max U32.
+ * min/max ignore NaN (IEEE minNum/maxNum).  Deterministic for a given
+ * (n, device): the combination order is fixed. */
+tr_status tr_reduce(const tr_map_desc* map, const void* d_x, tr_dtype xt, int64_t n, unsigned ops, void* d_sum,
+                    tr_dtype sum_t, void* d_min, void* d_max, const tr_exec* exec);
+
+/* ---- segmented reduction -------------------------------------------------- */
+
+tr_status tr_segmented_reduce_workspace_size(int64_t n, int64_t n_seg, tr_dtype xt, size_t* bytes);
+
+/* For each segment s < n_seg, elements [d_offsets[s], d_offsets[s+1]) of x:
+ * sum / min / max of f into d_sums[s], d_mins[s], d_maxs[s] (device arrays).
+ * d_offsets: n_seg + 1 int64 device values, offsets[0] = 0,
+ * offsets[n_seg] = n, non-decreasing; empty segments get the identities.
+ * Offsets that violate this are reported as TR_ERR_DEVICE_ASSERT by tr_check
+ * (results are then unspecified).  xt: F16, BF16, F32 (FP32 compute with
+ * compensated sums, FP64 combination of segment pieces); sum_t F32 or F64;
+ * mins/maxs F32.  Deterministic for a given (n, device). */
+tr_status tr_segmented_reduce(const tr_map_desc* map, const void* d_x, tr_dtype xt, int64_t n,
+                              const int64_t* d_offsets, int64_t n_seg, unsigned ops, void* d_sums, tr_dtype sum_t,
+                              void* d_mins, void* d_maxs, const tr_exec* exec);
+
+/* ---- inclusive scan ------------------------------------------------------- */
+
+tr_status tr_scan_workspace_size(int64_t n, tr_dtype xt, tr_dtype yt, size_t* bytes);
+
+/* y_i = f(x_0) + ... + f(x_i), single pass with decoupled look-back between
+ * tiles (Merrill & Garland, "Single-pass parallel prefix scan with decoupled
+ * look-back", NVIDIA NVR-2016-002).  Supported (xt -> yt):
+ *   U32 -> U32  modulo 2^32 (bit exact)
+ *   U32 -> U64  exact
+ *   F16/BF16/F32 -> F32  float-float within a tile, FP64 between tiles, each
+ *                 output rounded once from the compensated prefix.
+ * d_carry_in (nullable, device, one element of yt's type) is added to every
+ * output.  y may equal x when the element sizes match.  Each look-back wait
+ * is bounded by exec->wait_timeout_us; on expiry tr_check returns
+ * TR_ERR_TIMEOUT and the output is unspecified.  Float scans may differ in
+ * the last bit between runs (where the look-back stops depends on timing). */
+tr_status tr_scan(const tr_map_desc* map, const void* d_x, tr_dtype xt, void* d_y, tr_dtype yt, int64_t n,
+                  const void* d_carry_in, const tr_exec* exec);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TR_H */

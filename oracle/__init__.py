@@ -91,6 +91,7 @@ def _load():
             lib.orc_scan_u32.argtypes = [I32, P, P, I64]
             lib.orc_scan_u32_u64.argtypes = [I32, P, P, I64]
             lib.orc_scan_f64.argtypes = [P, P, P, I64, ctypes.c_int]
+            lib.orc_scan_f64_sampled.argtypes = [P, P, I64, P, I64, P, ctypes.c_int]
             lib.orc_vandermonde.argtypes = [P, P, I32, I64, P, I64, P, P]
             _lib = lib
     return _lib
@@ -204,6 +205,16 @@ def scan_float(m: MapSpec, x, p: int = 24) -> np.ndarray:
     c = m._c()
     _load().orc_scan_f64(ctypes.byref(c), _ptr(xd), _ptr(y), xd.size, int(p))
     return y
+
+
+def scan_float_sampled(m: MapSpec, x, positions, p: int = 24) -> np.ndarray:
+    """Exact inclusive prefixes of f at the given positions, each rounded once."""
+    xd = _f64(x)
+    pos = np.ascontiguousarray(np.sort(np.asarray(positions, dtype=np.int64)))
+    out = np.empty(pos.size, np.float64)
+    c = m._c()
+    _load().orc_scan_f64_sampled(ctypes.byref(c), _ptr(xd), xd.size, _ptr(pos), pos.size, _ptr(out), int(p))
+    return out
 
 
 def vandermonde(x, coef, rows=None, with_scale: bool = True):

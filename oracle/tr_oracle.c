@@ -290,6 +290,20 @@ void orc_scan_f64(const orc_map* m, const double* x, double* y, int64_t n, int p
   }
 }
 
+/* The same exact prefixes, rounded only at the sorted positions pos[0..m)
+ * (for checking very long scans at sampled outputs). */
+void orc_scan_f64_sampled(const orc_map* m, const double* x, int64_t n, const int64_t* pos, int64_t npos, double* out,
+                          int p) {
+  orc_acc a;
+  acc_clear(&a);
+  int qmin = p == 24 ? ORC_BIAS - 149 : 0;
+  int64_t k = 0;
+  for (int64_t i = 0; i < n && k < npos; ++i) {
+    acc_add(&a, map_f64(m, x[i]));
+    while (k < npos && pos[k] == i) out[k++] = acc_round(&a, p, qmin);
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Dense Vandermonde product                                                 */
 /* ------------------------------------------------------------------------ */

@@ -1,0 +1,66 @@
+// internal.h -- host-side helpers shared by the launchers of libtr.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace tr {
+
+struct DevInfo {
+  int device = -1;
+  int sm_count = 0;
+  int smem_optin = 0;
+};
+
+// Properties of the current device (queried once per device).
+const DevInfo& dev_info();
+
+// Record a failure for tr_last_error() on this thread and return `s`.
+tr_status fail(tr_status s, const char* fmt, ...);
+
+// Turn a CUDA error into TR_ERR_CUDA (TR_OK for cudaSuccess).
+tr_status cuda_status(cudaError_t e, const char* what);
+
+// Check the launch of the kernel just enqueued.
+inline tr_status launch_status(const char* what) { return cuda_status(cudaGetLastError(), what); }
+
+size_t dtype_size(tr_dtype t);
+
+inline bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Validate a map descriptor for the given input kind and fill kernel params.
+// int_input: u32 storage (mixers / identity only).
+tr_status make_map_params(const tr_map_desc* d, bool int_input, MapParams* P);
+
+// Resident blocks per SM of a kernel at a block size (cached per kernel).
+int blocks_per_sm(const void* kernel, int threads, size_t dyn_smem = 0);
+
+inline WsHeader* ws_header(const tr_exec* e) { return static_cast<WsHeader*>(e->workspace); }
+inline char* ws_body(const tr_exec* e) { return static_cast<char*>(e->workspace) + kWsHeader; }
+
+inline cudaStream_t stream_of(const tr_exec* e) { return static_cast<cudaStream_t>(e->stream); }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ---- launchers (one per kernel family) ------------------------------------
+size_t reduce_ws_bytes(int64_t n, tr_dtype xt);
+tr_status launch_reduce(const MapParams& P, const void* x, tr_dtype xt, int64_t n, unsigned ops, void* sum,
+                        tr_dtype sum_t, void* mn, void* mx, const tr_exec* e);
+
+tr_status launch_map(const MapParams& P, const void* x, tr_dtype xt, void* y, int64_t n, const tr_exec* e);
+
+size_t segreduce_ws_bytes(int64_t n, int64_t n_seg, tr_dtype xt);
+tr_status launch_segreduce(const MapParams& P, const void* x, tr_dtype xt, int64_t n, const int64_t* off,
+                           int64_t n_seg, unsigned ops, void* sums, tr_dtype sum_t, void* mins, void* maxs,
+                           const tr_exec* e);
+
+size_t scan_ws_bytes(int64_t n, tr_dtype xt, tr_dtype yt);
+tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, tr_dtype yt, int64_t n,
+                      const void* carry, const tr_exec* e);
+
+}  // namespace tr

@@ -1,0 +1,304 @@
+// k_scan.cu -- tr_scan: inclusive prefix sums of f(x) in one pass.
+//
+// Single-pass scan with decoupled look-back (Merrill & Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", NVR-2016-002):
+//   * each block takes a tile id from an atomic counter (dynamic ids: every
+//     tile's predecessors have already started, so waiting on them ends);
+//   * a thread owns kItems contiguous elements (128-bit loads), scans them
+//     serially, then warps scan lane totals with shuffles and the block scans
+//     warp totals in shared memory;
+//   * the tile publishes its aggregate (flag A), warp 0 looks back over up to
+//     32 predecessors at a time, summing aggregates until it meets an
+//     inclusive prefix (flag P), then publishes its own inclusive prefix;
+//   * every wait is bounded by a %globaltimer deadline and an abort word: on
+//     expiry the block records TR_ERR_TIMEOUT and finishes instead of hanging.
+// Tile flags carry a 30-bit call epoch, so no per-call reset is needed: the
+// block that draws the last tile id (all others have read the epoch before
+// drawing; release/acquire on the counter orders that) resets the counter
+// and advances the epoch for the next call.
+//
+// Arithmetic: u32 wraps modulo 2^32; u32 -> u64 is exact; float scans keep
+// float-float (hi, lo) pairs inside a tile, FP64 between tiles, and round each
+// output once from the compensated prefix.
+#include "dispatch.cuh"
+
+namespace tr {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // 4096 elements
+
+constexpr uint32_t kFlagA = 1, kFlagP = 2;
+
+// ---- per-output arithmetic -------------------------------------------------
+struct OpU32 {
+  using T = uint32_t;      // in-tile running value
+  using Carry = uint32_t;  // between tiles
+  using Out = uint32_t;
+  __device__ static T zero() { return 0u; }
+  __device__ static T lift(uint32_t v) { return v; }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static Carry to_carry(T a) { return a; }
+  __device__ static Carry cadd(Carry a, Carry b) { return a + b; }
+  __device__ static T shfl_up(T a, int d) { return __shfl_up_sync(kFull, a, d); }
+  __device__ static Carry shfl_xor_c(Carry a, int d) { return __shfl_xor_sync(kFull, a, d); }
+};
+
+struct OpU64 {
+  using T = unsigned long long;
+  using Carry = unsigned long long;
+  using Out = unsigned long long;
+  __device__ static T zero() { return 0ull; }
+  __device__ static T lift(uint32_t v) { return v; }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static Carry to_carry(T a) { return a; }
+  __device__ static Carry cadd(Carry a, Carry b) { return a + b; }
+  __device__ static T shfl_up(T a, int d) { return __shfl_up_sync(kFull, a, d); }
+  __device__ static Carry shfl_xor_c(Carry a, int d) { return __shfl_xor_sync(kFull, a, d); }
+};
+
+struct OpF32 {
+  using T = FF;
+  using Carry = double;
+  using Out = float;
+  __device__ static T zero() { return FF{0.f, 0.f}; }
+  __device__ static T add(T a, T b) { return ff_add(a, b); }
+  __device__ static Carry to_carry(T a) { return ff_to_double(a); }
+  __device__ static Carry cadd(Carry a, Carry b) { return a + b; }
+  __device__ static T shfl_up(T a, int d) { return FF{__shfl_up_sync(kFull, a.hi, d), __shfl_up_sync(kFull, a.lo, d)}; }
+  __device__ static Carry shfl_xor_c(Carry a, int d) { return __shfl_xor_sync(kFull, a, d); }
+};
+
+template <class Op>
+__device__ __forceinline__ typename Op::T warp_incl_scan(typename Op::T v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const typename Op::T o = Op::shfl_up(v, d);
+    if (lane >= d) v = Op::add(o, v);
+  }
+  return v;
+}
+
+template <class Op>
+__device__ __forceinline__ typename Op::Carry warp_sum_carry(typename Op::Carry v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = Op::cadd(v, Op::shfl_xor_c(v, d));
+  return v;
+}
+
+struct ScanWs {
+  uint32_t* flags;
+  void* agg;
+  void* incl;
+};
+
+template <class In, class F, class Op>
+__global__ void __launch_bounds__(kThreads) k_scan(const In* __restrict__ x, typename Op::Out* y, int64_t n, int vec_ok,
+                                                   const __grid_constant__ MapParams P, WsHeader* hdr, ScanWs ws,
+                                                   const typename Op::Out* carry_in, uint64_t timeout_ns,
+                                                   int64_t stall_tile) {
+  using S = Storage<In>;
+  using C = typename S::C;
+  using T = typename Op::T;
+  using Carry = typename Op::Carry;
+  using Out = typename Op::Out;
+  constexpr int V = S::kVec;
+  constexpr int kLoads = kItems / V;  // 128-bit loads per thread
+
+  __shared__ uint32_t s_tile, s_tag;
+  __shared__ T s_warp[kWarps];
+  __shared__ Carry s_prefix;
+
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    const uint32_t ep = ld_relaxed_u32(&hdr->epoch);
+    const uint32_t t = atom_add_acq_rel_u32(&hdr->tile_counter, 1u);
+    if (t == gridDim.x - 1) {  // every other block has drawn its id: reset for the next call
+      hdr->tile_counter = 0u;
+      hdr->epoch = ep + 1u;
+    }
+    s_tile = t;
+    s_tag = (ep & 0x3FFFFFFFu) << 2;
+  }
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const uint32_t tag = s_tag;
+  Carry* agg = static_cast<Carry*>(ws.agg);
+  Carry* incl = static_cast<Carry*>(ws.incl);
+
+  // ---- load and map kItems contiguous elements ----------------------------------
+  const F f = MakeMap<F>::make(P);
+  const int64_t base = tile * kTile + (int64_t)threadIdx.x * kItems;
+  const bool full = vec_ok && base + kItems <= n;
+  C v[kItems];
+  if (full) {
+    const uint4* xv = reinterpret_cast<const uint4*>(x + base);
+    uint4 raw[kLoads];
+#pragma unroll
+    for (int j = 0; j < kLoads; ++j) raw[j] = ld_cached(xv + j);
+#pragma unroll
+    for (int j = 0; j < kLoads; ++j) S::unpack(raw[j], v + j * V);
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) v[i] = f(v[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) v[i] = (base + i < n) ? f(S::cvt(x[base + i])) : C(0);
+  }
+
+  // ---- serial scan of the thread's items, then warp and block scans -------------
+  T run[kItems];
+  T acc = Op::zero();
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    if constexpr (std::is_same<Op, OpF32>::value) {  // TwoSum into (hi, lo); lo absorbs the errors
+      float s, e;
+      two_sum(acc.hi, v[i], s, e);
+      acc.hi = s;
+      acc.lo += e;
+    } else {
+      acc = Op::add(acc, Op::lift(v[i]));
+    }
+    run[i] = acc;
+  }
+  const T incl_lane = warp_incl_scan<Op>(acc, lane);
+  T excl_lane = Op::shfl_up(incl_lane, 1);
+  if (lane == 0) excl_lane = Op::zero();
+  if (lane == 31) s_warp[wid] = incl_lane;
+  __syncthreads();
+  T warp_off = Op::zero(), tile_tot = Op::zero();
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    if (w < wid) warp_off = Op::add(warp_off, s_warp[w]);
+    tile_tot = Op::add(tile_tot, s_warp[w]);
+  }
+
+  // ---- decoupled look-back (warp 0) ---------------------------------------------
+  if (wid == 0) {
+    const Carry aggregate = Op::to_carry(tile_tot);
+    const bool stall = (tile == stall_tile);
+    Carry excl = Carry(0);
+    if (tile == 0) {
+      if (lane == 0 && !stall) {
+        incl[0] = aggregate;
+        st_release_u32(&ws.flags[0], tag | kFlagP);
+      }
+    } else {
+      if (lane == 0 && !stall) {
+        agg[tile] = aggregate;
+        st_release_u32(&ws.flags[tile], tag | kFlagA);
+      }
+      const uint64_t deadline = globaltimer_ns() + timeout_ns;
+      int64_t pos = tile - 1;
+      bool aborted = false;
+      while (true) {
+        const int64_t idx = pos - lane;
+        uint32_t st = 0;
+        while (true) {
+          if (idx >= 0) {
+            const uint32_t fl = ld_acquire_u32(&ws.flags[idx]);
+            st = ((fl & ~3u) == tag) ? (fl & 3u) : 0u;
+          } else {
+            st = kFlagP;  // before tile 0: an inclusive prefix of 0
+          }
+          if (__all_sync(kFull, st != 0u)) break;
+          int give_up = 0;
+          if (lane == 0) give_up = (globaltimer_ns() > deadline) || (ld_relaxed_u32(&hdr->abort) != 0u);
+          if (__shfl_sync(kFull, give_up, 0)) {
+            if (lane == 0 && !ld_relaxed_u32(&hdr->abort)) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)tile);
+            aborted = true;
+            break;
+          }
+          __nanosleep(64);
+        }
+        if (aborted) break;
+        Carry val = Carry(0);
+        if (idx >= 0) val = (st == kFlagP) ? incl[idx] : agg[idx];
+        const unsigned pmask = __ballot_sync(kFull, st == kFlagP);
+        const int j = __ffs(pmask) - 1;  // nearest predecessor holding an inclusive prefix
+        excl = Op::cadd(excl, warp_sum_carry<Op>((pmask == 0u || lane <= j) ? val : Carry(0)));
+        if (pmask) break;
+        pos -= 32;
+      }
+      if (lane == 0 && !stall) {
+        incl[tile] = Op::cadd(excl, aggregate);
+        st_release_u32(&ws.flags[tile], tag | kFlagP);
+      }
+    }
+    if (lane == 0) {
+      Carry c0 = Carry(0);
+      if (carry_in) c0 = Carry(*carry_in);
+      s_prefix = Op::cadd(c0, excl);
+    }
+  }
+  __syncthreads();
+
+  // ---- outputs ---------------------------------------------------------------------
+  Out o[kItems];
+  if constexpr (std::is_same<Op, OpF32>::value) {
+    const FF basef = ff_add(ff_add(ff_from_double(s_prefix), warp_off), excl_lane);
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {  // base + run_i, rounded once
+      float s, e;
+      two_sum(basef.hi, run[i].hi, s, e);
+      o[i] = s + (e + (basef.lo + run[i].lo));
+    }
+  } else {
+    const T b = Op::add(Op::add((T)s_prefix, warp_off), excl_lane);
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) o[i] = Op::add(b, run[i]);
+  }
+  if (full) {
+    uint4* yv = reinterpret_cast<uint4*>(y + base);
+    constexpr int kPer = 16 / (int)sizeof(Out);
+    constexpr int kStores = kItems / kPer;
+#pragma unroll
+    for (int j = 0; j < kStores; ++j) st_stream(yv + j, pack16(o + j * kPer));
+  } else {
+#pragma unroll
+    for (int i = 0; i < kItems; ++i)
+      if (base + i < n) y[base + i] = o[i];
+  }
+}
+
+}  // namespace
+
+size_t scan_ws_bytes(int64_t n, tr_dtype, tr_dtype) {
+  const int64_t tiles = std::max<int64_t>(1, ceil_div(n, kTile));
+  const int64_t flags = ceil_div(tiles * 4, 256) * 256;
+  const int64_t vals = ceil_div(tiles * 8, 256) * 256;
+  return (size_t)(kWsHeader + flags + 2 * vals);
+}
+
+tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, tr_dtype yt, int64_t n, const void* carry,
+                      const tr_exec* e) {
+  const int64_t tiles = ceil_div(n, kTile);
+  if (tiles > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "too many tiles");
+  const int64_t flags_b = ceil_div(tiles * 4, 256) * 256;
+  const int64_t vals_b = ceil_div(tiles * 8, 256) * 256;
+  const ScanWs ws{reinterpret_cast<uint32_t*>(ws_body(e)), ws_body(e) + flags_b, ws_body(e) + flags_b + vals_b};
+  const uint64_t timeout_ns = (uint64_t)(e->wait_timeout_us ? e->wait_timeout_us : 1000000u) * 1000ull;
+  const int vec_ok = aligned_to(x, 16) && aligned_to(y, 16);
+  cudaStream_t st = stream_of(e);
+  WsHeader* hdr = ws_header(e);
+  const int64_t stall = e->debug_stall_tile;
+  auto go = [&](auto op_tag) {
+    using Op = decltype(op_tag);
+    return [&](auto in_tag, auto map_tag) -> tr_status {
+      using In = decltype(in_tag);
+      using F = decltype(map_tag);
+      k_scan<In, F, Op><<<(unsigned)tiles, kThreads, 0, st>>>(
+          static_cast<const In*>(x), static_cast<typename Op::Out*>(y), n, vec_ok, P, hdr, ws,
+          static_cast<const typename Op::Out*>(carry), timeout_ns, stall);
+      return launch_status("k_scan");
+    };
+  };
+  if (xt == TR_U32 && yt == TR_U32) return dispatch_u32_map(P, go(OpU32{}));
+  if (xt == TR_U32 && yt == TR_U64) return dispatch_u32_map(P, go(OpU64{}));
+  if (yt == TR_F32) return dispatch_float_storage(xt, P, go(OpF32{}));
+  return fail(TR_ERR_UNSUPPORTED, "scan %d -> %d", xt, yt);
+}
+
+}  // namespace tr

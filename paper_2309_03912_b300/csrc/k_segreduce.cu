@@ -1,0 +1,224 @@
+// k_segreduce.cu -- tr_segmented_reduce: sum / min / max of f per segment.
+//
+// Layout of the work: the array is cut into equal contiguous element ranges,
+// one per warp of a resident grid.  A warp finds the first segment touching
+// its range with a 32-ary search over the offsets (log32 dependent loads),
+// then walks the segments in order, keeping a window of 32 offsets in
+// registers (one per lane).  Each segment piece -- the intersection of a
+// segment with the range -- is reduced by the whole warp: 128-bit loads,
+// kUnroll vectors in flight per lane, the map in registers, Kahan-compensated
+// per-lane sums of pairwise vector sums, then a float-float warp butterfly.
+//   * a piece that is the whole segment is written out directly;
+//   * a piece cut by the range start (head) or end (tail) goes to a per-warp
+//     workspace slot as FP64, and the last block to finish (atomic ticket
+//     after a fence) joins each cut segment's pieces in warp order in FP64.
+// The combination order is fixed by the grid, so results are deterministic.
+// Offsets are checked while walking (monotone, within [0, n]); a violation is
+// reported through the workspace status word instead of faulting.
+#include "accum.cuh"
+#include "dispatch.cuh"
+
+namespace tr {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kUnroll = 4;
+constexpr int kMaxGrid = 2048;
+
+struct SegSlot {
+  long long seg;  // segment id, -1 = unused
+  double sum;
+  float mn, mx;
+  int32_t through;  // the piece covers the whole range (segment continues)
+  int32_t pad;
+};
+static_assert(sizeof(SegSlot) == 32, "slot size");
+
+// First index i in [0, m] with off[i] >= a (off non-decreasing, off[m] >= a),
+// found by the warp with 32-ary narrowing; every lane returns it.
+__device__ __forceinline__ int64_t warp_lower_bound(const int64_t* off, int64_t m, int64_t a, int lane) {
+  int64_t lo = 0, hi = m + 1;  // answer in [lo, hi)
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t p = lo + (int64_t)lane * step;
+    const bool ge = p < hi ? (__ldg(off + p) >= a) : true;
+    const unsigned mask = __ballot_sync(kFull, ge);
+    const int k = mask ? __ffs(mask) - 1 : 32;
+    const int64_t nlo = k == 0 ? lo : lo + (int64_t)(k - 1) * step + 1;
+    const int64_t nhi = imin<int64_t>(hi, lo + (int64_t)k * step + 1);
+    lo = nlo;
+    hi = imax<int64_t>(nhi, nlo + 1);
+  }
+  const int64_t p = lo + lane;
+  const bool ge = p < hi ? (__ldg(off + p) >= a) : true;
+  const unsigned mask = __ballot_sync(kFull, ge);
+  return lo + (mask ? __ffs(mask) - 1 : 0);
+}
+
+template <class In, class F>
+__device__ __forceinline__ Acc<float> reduce_piece(const In* __restrict__ x, int64_t pa, int64_t pb, int x_aligned,
+                                                   const F& f, int lane) {
+  using S = Storage<In>;
+  constexpr int V = S::kVec;
+  Acc<float> acc;
+  if (pa >= pb) return acc;
+  const int64_t va = (pa + V - 1) / V, vb = pb / V;
+  if (!x_aligned || va >= vb) {  // misaligned base, or under two vectors' worth: element-wise
+    for (int64_t i = pa + lane; i < pb; i += 32) acc.add(f(S::cvt(x[i])));
+    return acc;
+  }
+  if (pa + lane < va * V) acc.add(f(S::cvt(x[pa + lane])));      // head (< V elements)
+  if (vb * V + lane < pb) acc.add(f(S::cvt(x[vb * V + lane])));  // tail (< V elements)
+  const uint4* xv = reinterpret_cast<const uint4*>(x);
+  int64_t v = va + lane;
+  for (; v + 32 * (kUnroll - 1) < vb; v += 32 * kUnroll) {
+    uint4 raw[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) raw[u] = ld_stream(xv + v + 32 * u);
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      float e[V];
+      S::unpack(raw[u], e);
+#pragma unroll
+      for (int i = 0; i < V; ++i) e[i] = f(e[i]);
+      acc.template add_vec<V>(e);
+    }
+  }
+  for (; v < vb; v += 32) {
+    float e[V];
+    S::unpack(ld_stream(xv + v), e);
+#pragma unroll
+    for (int i = 0; i < V; ++i) e[i] = f(e[i]);
+    acc.template add_vec<V>(e);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ void write_slot(SegSlot* sl, long long seg, const Acc<float>::W& w, int through) {
+  sl->seg = seg;
+  sl->sum = ff_to_double(w.s);
+  sl->mn = w.mn;
+  sl->mx = w.mx;
+  sl->through = through;
+}
+
+template <class In, class F>
+__global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x, int64_t n,
+                                                        const int64_t* __restrict__ off, int64_t nseg, int64_t range,
+                                                        int x_aligned, const __grid_constant__ MapParams P,
+                                                        RedOut out, WsHeader* hdr, SegSlot* slots) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  const int64_t a = gw * range;
+  const int64_t b = imin<int64_t>(n, a + range);
+  const bool active = a < n || (n == 0 && gw == 0);
+  const bool last = active && b == n;
+  bool wrote_head = false, wrote_tail = false;
+
+  if (active) {
+    const F f = MakeMap<F>::make(P);
+    const int64_t i0 = warp_lower_bound(off, nseg, a, lane);
+    int64_t s = (i0 <= nseg && __ldg(off + i0) == a) ? i0 : i0 - 1;
+    if (s < 0) s = 0;
+    int64_t wbase = s;
+    int64_t win = (wbase + lane <= nseg) ? __ldg(off + wbase + lane) : n;
+    while (s < nseg) {
+      if (s + 1 - wbase >= 32) {
+        wbase = s;
+        win = (wbase + lane <= nseg) ? __ldg(off + wbase + lane) : n;
+      }
+      const int64_t lo_s = __shfl_sync(kFull, win, (int)(s - wbase));
+      const int64_t hi_s = __shfl_sync(kFull, win, (int)(s + 1 - wbase));
+      if (lo_s >= b && !(last && lo_s == n)) break;
+      if (hi_s < lo_s || lo_s < 0 || hi_s > n) {
+        if (lane == 0) set_status(hdr, TR_ERR_DEVICE_ASSERT, (uint32_t)s);
+        break;
+      }
+      const int64_t pa = imax(lo_s, a), pb = imin(hi_s, b);
+      const Acc<float> acc = reduce_piece<In, F>(x, pa, pb, x_aligned, f, lane);
+      const Acc<float>::W w = acc.warp();
+      const bool head_open = lo_s < a, tail_open = hi_s > b;
+      if (lane == 0) {
+        if (!head_open && !tail_open) {
+          store_result(out, s, Acc<float>::to_partial(w), true);
+        } else if (head_open) {
+          write_slot(&slots[2 * gw], s, w, tail_open ? 1 : 0);
+          wrote_head = true;
+        } else {
+          write_slot(&slots[2 * gw + 1], s, w, 0);
+          wrote_tail = true;
+        }
+      }
+      ++s;
+    }
+  }
+  if (lane == 0) {
+    if (!wrote_head) slots[2 * gw].seg = -1;
+    if (!wrote_tail) slots[2 * gw + 1].seg = -1;
+  }
+
+  // ---- the last block joins the pieces of cut segments -----------------------------
+  __shared__ bool last_block;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_block = atomicAdd(&hdr->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last_block) return;
+  __threadfence();
+  for (int64_t w = threadIdx.x; w < nw; w += kThreads) {
+    const long long sg = __ldcg(&slots[2 * w + 1].seg);
+    if (sg < 0) continue;
+    double sum = __ldcg(&slots[2 * w + 1].sum);
+    float mn = __ldcg(&slots[2 * w + 1].mn), mx = __ldcg(&slots[2 * w + 1].mx);
+    for (int64_t w2 = w + 1; w2 < nw; ++w2) {
+      const SegSlot* h = &slots[2 * w2];
+      if (__ldcg(&h->seg) != sg) {
+        set_status(hdr, TR_ERR_DEVICE_ASSERT, (uint32_t)sg);
+        break;
+      }
+      sum += __ldcg(&h->sum);
+      mn = fminf(mn, __ldcg(&h->mn));
+      mx = fmaxf(mx, __ldcg(&h->mx));
+      if (!__ldcg(&h->through)) break;
+    }
+    store_result(out, sg, PartialF{sum, (double)mn, (double)mx}, true);
+  }
+  if (threadIdx.x == 0) hdr->ticket = 0;
+}
+
+}  // namespace
+
+size_t segreduce_ws_bytes(int64_t, int64_t, tr_dtype) {
+  return kWsHeader + (size_t)kMaxGrid * kWarps * 2 * sizeof(SegSlot);
+}
+
+tr_status launch_segreduce(const MapParams& P, const void* x, tr_dtype xt, int64_t n, const int64_t* off,
+                           int64_t n_seg, unsigned ops, void* sums, tr_dtype sum_t, void* mins, void* maxs,
+                           const tr_exec* e) {
+  const RedOut out{sums, mins, maxs, (int32_t)sum_t, ops};
+  cudaStream_t st = stream_of(e);
+  const int x_aligned = aligned_to(x, 16);
+  return dispatch_float_storage(xt, P, [&](auto in_tag, auto map_tag) -> tr_status {
+    using In = decltype(in_tag);
+    using F = decltype(map_tag);
+    constexpr int V = Storage<In>::kVec;
+    auto kern = k_segreduce<In, F>;
+    const int64_t resident = (int64_t)dev_info().sm_count * blocks_per_sm((const void*)kern, kThreads);
+    const int64_t grid_full = std::min<int64_t>(resident, kMaxGrid);
+    const int64_t quantum = 32 * V;  // range starts stay 16-byte aligned
+    int64_t range = ceil_div(std::max<int64_t>(n, 1), grid_full * kWarps);
+    range = ceil_div(range, quantum) * quantum;
+    const int64_t warps_needed = std::max<int64_t>(1, ceil_div(n, range));
+    const int64_t grid = ceil_div(warps_needed, kWarps);
+    kern<<<(unsigned)grid, kThreads, 0, st>>>(static_cast<const In*>(x), n, off, n_seg, range, x_aligned, P, out,
+                                               ws_header(e), reinterpret_cast<SegSlot*>(ws_body(e)));
+    return launch_status("k_segreduce");
+  });
+}
+
+}  // namespace tr

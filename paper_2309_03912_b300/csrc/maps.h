@@ -1,0 +1,129 @@
+// maps.h -- the map family f, written once for host, device and compile time.
+//
+// Every functor is TR_HD + constexpr and declares `hdc = HDC::HstDev`, the
+// host-device-compatibility tag of the paper's Sec. 4 helper; the
+// compile-time checks assert tr::hdc<F> == HDC::HstDev for the whole family.
+// The operation sequence of each map is fixed (explicit fused multiply-adds,
+// one IEEE division where a quotient appears) so that host code compiled with
+// -ffp-contract=off, device code compiled with -fmad=false and constant
+// evaluation on exactly representable inputs give identical bits.
+//
+//   Horner     p = c_d; p = fma(p, x, c_k), k = d-1 .. 0 (ascending c)
+//   Rational   P(x) / Q(x), both by Horner
+//   NewtonCbrt y_0 = sign(x); y <- (2y + x / (y*y)) / 3, a fixed number of
+//              steps; the result is the iterate (not cbrt(x))
+//   Square     x * x
+//   Xorshift32 Marsaglia, "Xorshift RNGs" (2003), shift triple 13/17/5
+//   Splitmix32 Weyl increment floor(2^32/phi), then (z ^ z>>16) * m1,
+//              (z ^ z>>13) * m2, z ^ z>>16 with m1, m2 the first 32 bits of
+//              the fractional parts of sqrt(2) and sqrt(3), all mod 2^32
+#pragma once
+
+#include "hd.h"
+
+namespace tr {
+
+template <class T>
+struct Identity {
+  static constexpr HDC hdc = HDC::HstDev;
+  TR_HD constexpr T operator()(T x) const { return x; }
+};
+
+template <class T>
+struct Square {
+  static constexpr HDC hdc = HDC::HstDev;
+  TR_HD constexpr T operator()(T x) const { return x * x; }
+};
+
+// Horner's rule on d+1 ascending coefficients held anywhere addressable.
+template <class T>
+TR_HD constexpr T horner_eval(const T* c, int d, T x) {
+  T p = c[d];
+  for (int k = d - 1; k >= 0; --k) p = fma_hd(p, x, c[k]);
+  return p;
+}
+
+// Compile-time degree D: coefficients by value (registers on the device).
+template <class T, int D>
+struct Horner {
+  static constexpr HDC hdc = HDC::HstDev;
+  T c[D + 1];
+  TR_HD constexpr T operator()(T x) const {
+    T p = c[D];
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) p = fma_hd(p, x, c[k]);
+    return p;
+  }
+};
+
+// Run-time degree: coefficients by pointer.
+template <class T>
+struct HornerN {
+  static constexpr HDC hdc = HDC::HstDev;
+  const T* c;
+  int d;
+  TR_HD constexpr T operator()(T x) const { return horner_eval(c, d, x); }
+};
+
+template <class T, int DP, int DQ>
+struct Rational {
+  static constexpr HDC hdc = HDC::HstDev;
+  T p[DP + 1];
+  T q[DQ + 1];
+  TR_HD constexpr T operator()(T x) const {
+    T a = p[DP];
+#pragma unroll
+    for (int k = DP - 1; k >= 0; --k) a = fma_hd(a, x, p[k]);
+    T b = q[DQ];
+#pragma unroll
+    for (int k = DQ - 1; k >= 0; --k) b = fma_hd(b, x, q[k]);
+    return a / b;
+  }
+};
+
+template <class T>
+struct RationalN {
+  static constexpr HDC hdc = HDC::HstDev;
+  const T* p;
+  const T* q;
+  int dp, dq;
+  TR_HD constexpr T operator()(T x) const { return horner_eval(p, dp, x) / horner_eval(q, dq, x); }
+};
+
+// ITERS >= 0: fixed step count; ITERS < 0: run-time count in `iters`.
+template <class T, int ITERS>
+struct NewtonCbrt {
+  static constexpr HDC hdc = HDC::HstDev;
+  int iters = ITERS;
+  TR_HD constexpr T operator()(T x) const {
+    T y = copysign_one(x);
+    const int n = ITERS >= 0 ? ITERS : iters;
+    for (int k = 0; k < n; ++k) y = (T(2) * y + x / (y * y)) / T(3);
+    return y;
+  }
+};
+
+struct Xorshift32 {
+  static constexpr HDC hdc = HDC::HstDev;
+  TR_HD constexpr uint32_t operator()(uint32_t x) const {
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    return x;
+  }
+};
+
+struct Splitmix32 {
+  static constexpr HDC hdc = HDC::HstDev;
+  static constexpr uint32_t kWeyl = 0x9E3779B9u;  // floor(2^32 / golden ratio)
+  static constexpr uint32_t kM1 = 0x6A09E667u;    // frac(sqrt 2) * 2^32
+  static constexpr uint32_t kM2 = 0xBB67AE85u;    // frac(sqrt 3) * 2^32
+  TR_HD constexpr uint32_t operator()(uint32_t x) const {
+    uint32_t z = x + kWeyl;
+    z = (z ^ (z >> 16)) * kM1;
+    z = (z ^ (z >> 13)) * kM2;
+    return z ^ (z >> 16);
+  }
+};
+
+}  // namespace tr

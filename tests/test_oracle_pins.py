@@ -362,3 +362,13 @@ def test_vandermonde_dyadic_column_sums(orc):
     Y = orc.vandermonde(x, C, with_scale=False)
     for j in range(2):
         assert math.fsum(Y[:, j]) == float(_dyadic_poly_sum(C[:, j].tolist(), N))
+
+
+def test_scan_sampled_matches_full_scan(orc):
+    """The sampled prefix routine returns exactly the full scan's values."""
+    g = np.random.default_rng(16)
+    x = g.uniform(0, 1, 20000).astype(np.float32)
+    m = orc.MapSpec("square")
+    full = orc.scan_float(m, x, 24)
+    pos = np.sort(g.choice(x.size, 300, replace=False))
+    assert np.array_equal(orc.scan_float_sampled(m, x, pos, 24), full[pos])
