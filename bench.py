@@ -1,0 +1,470 @@
+#!/usr/bin/env python
+"""Benchmark of the transform-reduce-scan path on B300.
+
+One step = one pass of the hot path over the headline workload: the segmented
+transform-reduce of N = 2^28 f32 values x ~ N(0,1) through the rational map
+P/Q of degree 6/6 (Q with positive even coefficients, no poles) into 65,536
+segments (lengths U{1..8192} rescaled to N): per segment a compensated sum
+(FP64 output), min and max -- load, map, accumulate, combine, all in one
+tr_segmented_reduce launch.  Inputs (1 GiB) exceed the 126 MB L2, so no flush
+is needed between steps.
+
+Prints ONE JSON line (rank 0).  Besides the headline it reports, under
+"configs", the other workloads of the path measured the same way (FP64 and
+u32 reductions, u32/u64/f32 scans, FP16-storage reduction).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tr|reference]
+
+--impl reference times the CPU oracle (this project's reference arm: the plain
+FP64 / exact-summation C implementation) on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("elements/s and HBM GB/s (% of ~8 TB/s) for transform-reduce/scan; "
+          "batched vs plain speedup at tol")
+NOMINAL_HBM_GBS = 8000.0
+N_HEAD = 1 << 28
+NSEG_HEAD = 65536
+WORKLOAD = ("segmented transform-reduce: N=2^28 f32 x~N(0,1), f = rational P/Q deg 6/6 (Q even, positive "
+            "coefficients), 65536 segments with lengths U{1..8192} scaled to N; per segment compensated "
+            "sum (f64 out), min, max")
+SEG_SOURCES = ["paper_2309_03912_b300/csrc/k_segreduce.cu", "paper_2309_03912_b300/csrc/accum.cuh",
+               "paper_2309_03912_b300/csrc/common.cuh", "paper_2309_03912_b300/csrc/maps.h"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="tr", choices=["tr", "reference"])
+    p.add_argument("--no-configs", action="store_true", help="headline only")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- utilities
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6400.0, 1800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = [[s.strip() for s in line.split(",")] for line in open(self.path)]
+        rows = [r for r in rows if len(r) >= 9]
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        pw = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": num(rows[0][2]),
+                "power_w_max": max(pw) if pw else None, "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def source_sha(sources):
+    h = hashlib.sha256()
+    for s in sources:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel: str, sources: list[str]):
+    """DRAM bytes per launch from an ncu capture summarised in profiles/, valid
+    only while the kernel's sources are unchanged (their sha256 is stored there)."""
+    sha = source_sha(sources)
+    for p in glob.glob(os.path.join(ROOT, "profiles", f"{kernel}*.md")):
+        txt = open(p).read()
+        ms = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
+        mt = re.search(r"traffic_bytes_per_launch:\s*([0-9.e+]+)", txt)
+        mn = re.search(r"traffic_n:\s*([0-9]+)", txt)
+        if ms and mt and ms.group(1) == sha:
+            return float(mt.group(1)), (int(mn.group(1)) if mn else None), sha
+    return None, None, sha
+
+
+def time_launches(fn, steps, warmup, stream):
+    """Device time per call (ms): CUDA events on `stream` between calls."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for i in range(steps):
+            fn()
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+    return statistics.mean(per), min(per), per
+
+
+def time_graph(fn, reps, stream, replays=10):
+    """Device time per call (ms) of `fn` captured `reps` times into one CUDA
+    graph (the C-ABI calls allocate and synchronise nothing, so they capture),
+    replayed `replays` times between CUDA events.  Used for the small sizes,
+    whose kernels are shorter than a host launch."""
+    import torch
+    with torch.cuda.stream(stream):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(reps):
+                fn()
+        g.replay()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(replays):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+    return a.elapsed_time(b) / (replays * reps)
+
+
+# ----------------------------------------------------------------------------- headline
+
+def headline(args, rank, world, stream):
+    import torch
+
+    from paper_2309_03912_b300 import binding as B
+    from paper_2309_03912_b300 import inputs as I
+
+    x, m, off = I.rational_segments(N_HEAD, NSEG_HEAD, salt=rank)
+    n, nseg = x.size, off.size - 1
+    xd = torch.from_numpy(x).cuda()
+    offd = torch.from_numpy(off).cuda()
+    sums = torch.empty(nseg, dtype=torch.float64, device="cuda")
+    mins = torch.empty(nseg, dtype=torch.float32, device="cuda")
+    maxs = torch.empty(nseg, dtype=torch.float32, device="cuda")
+    ws = B.workspace(B.tr_segmented_reduce_workspace_size(n, nseg, B.TR_F32))
+    ex = B.make_exec(ws, stream=stream)
+    ops = B.TR_SUM | B.TR_MIN | B.TR_MAX
+    md = B.MapDesc(m)
+    L = B.lib()
+    exr = ctypes.byref(ex)
+
+    def step():
+        st = L.tr_segmented_reduce(md.ref(), xd.data_ptr(), B.TR_F32, n, offd.data_ptr(), nseg, ops,
+                                   sums.data_ptr(), B.TR_F64, mins.data_ptr(), maxs.data_ptr(), exr)
+        if st:
+            raise B.TrError(st, L.tr_last_error().decode())
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        B.tr_check(ex)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clk = Clocks(torch.cuda.current_device())
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        with clk:
+            evs[0].record(stream)
+            for i in range(args.steps):
+                step()
+                evs[i + 1].record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        B.tr_check(ex)
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        total_ms = evs[0].elapsed_time(evs[-1])
+        if world > 1:
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(t.item())
+
+        # end to end through the public API: pinned host input in, results out, every step
+        xh = torch.from_numpy(x).pin_memory()
+        offh = torch.from_numpy(off).pin_memory()
+        sums_h = torch.empty(nseg, dtype=torch.float64).pin_memory()
+        mins_h = torch.empty(nseg, dtype=torch.float32).pin_memory()
+        maxs_h = torch.empty(nseg, dtype=torch.float32).pin_memory()
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            offd.copy_(offh, non_blocking=True)
+            step()
+            sums_h.copy_(sums, non_blocking=True)
+            mins_h.copy_(mins, non_blocking=True)
+            maxs_h.copy_(maxs, non_blocking=True)
+
+        e2e_ms, _, _ = time_launches(e2e_step, max(3, min(args.steps, 10)), 2, stream)
+        B.tr_check(ex)
+    return {"n": n, "nseg": nseg, "per_ms": per, "total_ms": total_ms, "clocks": clk.summary(),
+            "alg_bytes": n * 4 + (nseg + 1) * 8 + nseg * 16, "e2e_ms": e2e_ms,
+            "h2d": n * 4 + (nseg + 1) * 8, "d2h": nseg * 16}
+
+
+# ----------------------------------------------------------------------------- other workloads
+
+def other_configs(args, stream, hbm_peak):
+    import numpy as np
+    import torch
+
+    from paper_2309_03912_b300 import binding as B
+    from paper_2309_03912_b300 import inputs as I
+
+    out = {}
+    steps, warm = max(5, min(args.steps, 20)), 3
+
+    def record(name, ms, n, nbytes, launches, extra=None):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        d = {"ms": round(ms, 5), "elements_per_s": n / (ms * 1e-3), "alg_bytes": nbytes, "hbm_gbs": round(gbs, 1),
+             "frac_of_measured_hbm": round(gbs / hbm_peak, 4), "frac_of_8tbs": round(gbs / NOMINAL_HBM_GBS, 4),
+             "launches_per_step": launches}
+        d.update(extra or {})
+        out[name] = d
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2, for the L2-resident sizes
+
+    # plain FP64 Horner reduce, N = 2^20 (L2-resident: timed as graph replays of 20 calls,
+    # with and without an L2 flush before each call)
+    x, m = I.horner_f64(1 << 20)
+    xd = torch.from_numpy(x).cuda()
+    ws = B.workspace(B.tr_reduce_workspace_size(x.size, B.TR_F64))
+    s = torch.empty(3, dtype=torch.float64, device="cuda")
+    f = lambda: B.tr_reduce(m, xd, 7, s[0:1], s[1:2], s[2:3], B.make_exec(ws))
+    ms = time_graph(f, 20, stream)
+    ms_flush = time_graph(lambda: (flush.zero_(), f()), 20, stream) - time_graph(lambda: flush.zero_(), 20, stream)
+    record("reduce_f64_horner8_2^20", ms, x.size, x.nbytes, 1,
+           {"ms_after_l2_flush": round(ms_flush, 5), "timing": "cuda graph of 20 calls",
+            "bound": "FP64 ALU (B300 FP64 is ~1/64 of FP32) and launch latency"})
+
+    # u32 xorshift32: exact u64 sum + u32 -> u64 inclusive scan, N = 2^20
+    xu = I.mixer_u32(1 << 20)
+    xud = torch.from_numpy(xu.view(np.int32)).cuda()
+    wsr = B.workspace(B.tr_reduce_workspace_size(xu.size, B.TR_U32))
+    wss = B.workspace(B.tr_scan_workspace_size(xu.size, B.TR_U32, B.TR_U64))
+    s64 = torch.empty(1, dtype=torch.int64, device="cuda")
+    y64 = torch.empty(xu.size, dtype=torch.int64, device="cuda")
+
+    def c1b():
+        B.tr_reduce({"kind": "xorshift32"}, xud, 1, s64, None, None, B.make_exec(wsr))
+        B.tr_scan({"kind": "xorshift32"}, xud, y64, B.make_exec(wss))
+    ms = time_graph(c1b, 20, stream)
+    record("sum_u64_and_scan_u64_xorshift32_2^20", ms, xu.size, xu.nbytes * 2 + y64.numel() * 8, 2,
+           {"timing": "cuda graph of 20 calls"})
+    del xud, y64
+
+    # u32 splitmix32 inclusive scan mod 2^32, N = 2^28
+    xu = I.mixer_u32(1 << 28, stream="mixer_u32_scan")
+    xud = torch.from_numpy(xu.view(np.int32)).cuda()
+    del xu
+    y = torch.empty_like(xud)
+    wss = B.workspace(B.tr_scan_workspace_size(xud.numel(), B.TR_U32, B.TR_U32))
+    exs = B.make_exec(wss, stream=stream)
+    ms, _, _ = time_launches(lambda: B.tr_scan({"kind": "splitmix32"}, xud, y, exs), steps, warm, stream)
+    record("scan_u32_splitmix32_2^28", ms, xud.numel(), xud.numel() * 8, 1)
+    del xud, y
+
+    # f32 compensated scan of x^2, N = 2^28
+    xf = I.square_f32(1 << 28)
+    xfd = torch.from_numpy(xf).cuda()
+    del xf
+    y = torch.empty_like(xfd)
+    wss = B.workspace(B.tr_scan_workspace_size(xfd.numel(), B.TR_F32, B.TR_F32))
+    exs = B.make_exec(wss, stream=stream)
+    ms, _, _ = time_launches(lambda: B.tr_scan(I.simple_map("square"), xfd, y, exs), steps, warm, stream)
+    record("scan_f32_square_compensated_2^28", ms, xfd.numel(), xfd.numel() * 8, 1)
+    del xfd, y
+
+    # FP16 storage, FP32 compute: Horner deg 8 sum/min/max, N = 2^30
+    xh, m = I.horner_f16(1 << 30)
+    xhd = torch.from_numpy(xh).cuda()
+    del xh
+    ws = B.workspace(B.tr_reduce_workspace_size(xhd.numel(), B.TR_F16))
+    ex = B.make_exec(ws, stream=stream)
+    s = torch.empty(1, dtype=torch.float64, device="cuda")
+    mm = torch.empty(2, dtype=torch.float32, device="cuda")
+    ms16, _, _ = time_launches(lambda: B.tr_reduce(m, xhd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
+    record("reduce_f16_storage_horner8_2^30", ms16, xhd.numel(), xhd.numel() * 2, 1)
+    # the same values in f32 storage: the plain FP32 comparison for the mixed-precision form
+    xfd = xhd.float()
+    del xhd
+    ws = B.workspace(B.tr_reduce_workspace_size(xfd.numel(), B.TR_F32))
+    ex = B.make_exec(ws, stream=stream)
+    ms32, _, _ = time_launches(lambda: B.tr_reduce(m, xfd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
+    record("reduce_f32_storage_horner8_2^30", ms32, xfd.numel(), xfd.numel() * 4, 1,
+           {"f16_storage_speedup": round(ms32 / ms16, 3)})
+    del xfd
+    B.tr_check(ex)
+    torch.cuda.synchronize()
+    return out
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(target_elems: int = N_HEAD, repeats: int = 1):
+    """Time the oracle (as it stands, one host thread) on the first segments of
+    the headline workload holding about target_elems elements, `repeats`
+    times.  Returns (cpu_baseline record, seconds per repeat, elements)."""
+    import numpy as np
+
+    import oracle
+    from paper_2309_03912_b300 import inputs as I
+
+    x, m, off = I.rational_segments(N_HEAD, NSEG_HEAD)
+    k = max(1, min(int(np.searchsorted(off, target_elems)), off.size - 1))
+    sub_off = np.ascontiguousarray(off[:k + 1])
+    nel = int(sub_off[-1])
+    xs = np.ascontiguousarray(x[:nel])
+    del x
+    spec = oracle.MapSpec(m["kind"], m["cp"], m["cq"])
+    oracle.build()
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.segmented_reduce_float(spec, xs, sub_off)
+        times.append(time.perf_counter() - t0)
+    dt = statistics.mean(times)
+    return ({"value": nel / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+             "sample": f"first {k} of {NSEG_HEAD} segments ({nel} of {N_HEAD} elements), one host thread, "
+                       f"{dt:.2f} s per pass, {repeats} pass(es)"}, times, nel)
+
+
+# ----------------------------------------------------------------------------- main
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        # warm-up passes on a small sample, then each step: the oracle over ~2^23 elements (~0.4 s)
+        oracle_sample(1 << 20, repeats=max(1, args.warmup))
+        cb, times, nel = oracle_sample(1 << 23, repeats=args.steps)
+        line = {"metric": METRIC, "value": cb["value"], "unit": "elements/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD, "n": N_HEAD, "n_seg": NSEG_HEAD, "step_sample_elements": nel,
+                           "parallelism": "host, one thread"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2309_03912_b300 import binding as B
+    from paper_2309_03912_b300 import build as Bd
+    if not os.path.exists(B.LIB_PATH):
+        Bd.build()
+    B.lib()
+    hbm_peak, _, peak_src = peaks()
+    stream = torch.cuda.Stream()
+
+    h = headline(args, rank, world, stream)
+    configs = None if (args.no_configs or rank != 0) else other_configs(args, stream, hbm_peak)
+    cb = oracle_sample()[0] if (rank == 0 and world == 1 and not args.no_cpu) else None
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
+
+    ms_step = h["total_ms"] / args.steps
+    kern_ms = statistics.mean(h["per_ms"])
+    achieved = h["alg_bytes"] / (kern_ms * 1e-3) / 1e9
+    traffic, traffic_n, sha = profile_traffic("k_segreduce", SEG_SOURCES)
+    if traffic is not None and traffic_n:
+        traffic = traffic * h["n"] / traffic_n
+    line = {
+        "metric": METRIC, "value": world * h["n"] / (ms_step * 1e-3), "unit": "elements/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": h["n"], "n_seg": h["nseg"], "map": "rational 6/6",
+                   "l2": "inputs (1 GiB) larger than L2 (126 MB); no flush", "parallelism": f"replicas x{world}"},
+        "hbm_gbs": round(achieved, 1), "frac_of_8tbs": round(achieved / NOMINAL_HBM_GBS, 4),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(achieved / hbm_peak, 4), "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "k_segreduce<float, Rational<float,6,6>>", "alg_bytes_per_launch": h["alg_bytes"],
+                     "kernel_ms": round(kern_ms, 5), "source_sha": sha},
+        "e2e": {"value": world * h["n"] / (h["e2e_ms"] * 1e-3), "unit": "elements/s",
+                "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"]},
+        "gpu_launches": args.steps,
+        "clocks": h["clocks"],
+        "cpu_baseline": cb,
+        "configs": configs,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
