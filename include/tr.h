@@ -186,6 +186,29 @@ tr_status tr_scan_workspace_size(int64_t n, tr_dtype xt, tr_dtype yt, size_t* by
 tr_status tr_scan(const tr_map_desc* map, const void* d_x, tr_dtype xt, void* d_y, tr_dtype yt, int64_t n,
                   const void* d_carry_in, const tr_exec* exec);
 
+/* ---- inclusive scan without a workspace -------------------------------------- */
+
+/* The scan of tr_scan (same dtypes, maps, arithmetic and results) for callers
+ * that cannot allocate device memory -- for example code running inside a
+ * memory allocator, plugins handed only input and output pointers, or loops
+ * that must not allocate once started -- and so cannot provide a workspace.
+ * The paper has no counterpart to this entry point.
+ *
+ * The scratch lives in one fixed device array inside the library (about
+ * 320 KiB, reserved on every GPU that loads the library and held until the
+ * process exits), so n is limited to 2^26 elements; larger n is rejected with
+ * TR_ERR_INVALID_ARG and a message naming the limit.  The call makes no
+ * allocation of any kind.  Its first call on a device looks up the array's
+ * device address for that device; make that first call before any stream
+ * capture.  Every call shares the one array, so calls that may overlap on the
+ * GPU (other streams, other host threads) race and must be serialised by the
+ * caller.  The error words of the array are cleared at the start of each call.
+ * d_status (nullable, device, one uint32) receives the device-side status of
+ * this call: 0, or TR_ERR_TIMEOUT if a look-back wait ran out (1 s bound).
+ * stream: cudaStream_t, NULL = legacy default stream. */
+tr_status tr_scan_noalloc(const tr_map_desc* map, const void* d_x, tr_dtype xt, void* d_y, tr_dtype yt, int64_t n,
+                          const void* d_carry_in, uint32_t* d_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

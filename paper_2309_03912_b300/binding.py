@@ -70,6 +70,7 @@ SIGNATURES = {
     "tr_segmented_reduce": ([_M, _P, _I32, _I64, _P, _I64, _U32, _P, _I32, _P, _P, _E], _I32),
     "tr_scan_workspace_size": ([_I64, _I32, _I32, ctypes.POINTER(_SZ)], _I32),
     "tr_scan": ([_M, _P, _I32, _P, _I32, _I64, _P, _E], _I32),
+    "tr_scan_noalloc": ([_M, _P, _I32, _P, _I32, _I64, _P, _P, _P], _I32),
 }
 
 
@@ -194,3 +195,12 @@ def tr_scan(m: dict, x: torch.Tensor, y: torch.Tensor, ex: tr_exec, carry_in: to
     md = MapDesc(m)
     _check(lib().tr_scan(md.ref(), _ptr(x), dtype_of(x), _ptr(y), dtype_of(y), x.numel(), _ptr(carry_in),
                          ctypes.byref(ex)))
+
+
+def tr_scan_noalloc(m: dict, x: torch.Tensor, y: torch.Tensor, status: torch.Tensor | None = None,
+                    carry_in: torch.Tensor | None = None, stream=None) -> None:
+    """tr_scan without a workspace (fixed library scratch, n <= 2^26)."""
+    md = MapDesc(m)
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib().tr_scan_noalloc(md.ref(), _ptr(x), dtype_of(x), _ptr(y), dtype_of(y), x.numel(), _ptr(carry_in),
+                                 _ptr(status), s))
