@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--impl", default="tr", choices=["tr", "reference"])
     p.add_argument("--no-configs", action="store_true", help="headline only")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    p.add_argument("--head-n", type=int, default=N_HEAD,
+                   help="elements of the headline workload (segments scale with it); smaller sizes are "
+                        "for profiler captures only")
     return p.parse_args()
 
 
@@ -198,7 +201,8 @@ def headline(args, rank, world, stream):
     from paper_2309_03912_b300 import binding as B
     from paper_2309_03912_b300 import inputs as I
 
-    x, m, off = I.rational_segments(N_HEAD, NSEG_HEAD, salt=rank)
+    nseg_req = max(1, round(NSEG_HEAD * args.head_n / N_HEAD))
+    x, m, off = I.rational_segments(args.head_n, nseg_req, salt=rank)
     n, nseg = x.size, off.size - 1
     xd = torch.from_numpy(x).cuda()
     offd = torch.from_numpy(off).cuda()
