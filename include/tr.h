@@ -11,6 +11,7 @@
  *     sum / min / max of f over the array        tr_reduce
  *     the same per segment [off[s], off[s+1])    tr_segmented_reduce
  *     inclusive prefix sums of f                 tr_scan
+ *     thousands of arrays, mixed maps, one graph tr_batched_*
  *
  * Conventions (all entry points):
  *   - Every pointer named d_* or documented "device" is CUDA device memory
@@ -185,6 +186,43 @@ tr_status tr_scan_workspace_size(int64_t n, tr_dtype xt, tr_dtype yt, size_t* by
  * the last bit between runs (where the look-back stops depends on timing). */
 tr_status tr_scan(const tr_map_desc* map, const void* d_x, tr_dtype xt, void* d_y, tr_dtype yt, int64_t n,
                   const void* d_carry_in, const tr_exec* exec);
+
+/* ---- batched reduction ------------------------------------------------------ */
+
+typedef struct tr_batch_plan tr_batch_plan; /* opaque, owned by the library */
+
+/* Plan the reduction of n_arrays independent f32 device arrays, each with its
+ * own map (FP32 compute; Horner, rational, Newton cube root, square,
+ * identity), in ONE persistent kernel launch replayed from a CUDA graph.
+ *   d_xs[i]   (host array of device pointers) array i, lens[i] elements
+ *   maps[i]   its map (host descriptors, copied)
+ *   d_sums / d_mins / d_maxs  device arrays of n_arrays F64 / F32 / F32
+ *             (those selected by ops must be non-NULL)
+ * Each array is cut into work items; warps pull items from an atomic queue
+ * (longest first), reduce them with compensated FP32 sums, and the warp that
+ * finishes an array's last item joins its partials in FP64 in item order, so
+ * results are bitwise deterministic.  autotune != 0 times tile and block-size
+ * candidates on this data (it writes the outputs and synchronises the device;
+ * TR_AUTOTUNE_CACHE names an optional cache file); 0 takes a fixed default.
+ * Plan creation allocates the plan's device buffers and instantiates the
+ * graph; the arrays and outputs must stay valid while the plan is used. */
+tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, const int64_t* lens,
+                                 const tr_map_desc* maps, unsigned ops, double* d_sums, float* d_mins,
+                                 float* d_maxs, int autotune, void* stream, tr_batch_plan** out);
+
+/* Launch the plan's graph on stream (one cudaGraphLaunch).  Runs of one plan
+ * must not overlap on the GPU. */
+tr_status tr_batched_run(tr_batch_plan* plan, void* stream);
+
+/* The unbatched baseline: the same results with one tr_reduce launch per
+ * array; use_graph != 0 records those launches into a graph on first use and
+ * replays it.  Allocates the baseline's workspace on first use. */
+tr_status tr_batched_run_unbatched(tr_batch_plan* plan, int use_graph, void* stream);
+
+/* Text describing the chosen tile, block size, grid and item count. */
+const char* tr_batched_plan_describe(const tr_batch_plan* plan);
+
+tr_status tr_batched_plan_destroy(tr_batch_plan* plan);
 
 /* ---- inclusive scan without a workspace -------------------------------------- */
 

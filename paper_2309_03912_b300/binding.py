@@ -71,6 +71,11 @@ SIGNATURES = {
     "tr_scan_workspace_size": ([_I64, _I32, _I32, ctypes.POINTER(_SZ)], _I32),
     "tr_scan": ([_M, _P, _I32, _P, _I32, _I64, _P, _E], _I32),
     "tr_scan_noalloc": ([_M, _P, _I32, _P, _I32, _I64, _P, _P, _P], _I32),
+    "tr_batched_plan_create": ([_I64, _P, _P, _M, _U32, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)], _I32),
+    "tr_batched_run": ([_P, _P], _I32),
+    "tr_batched_run_unbatched": ([_P, _I32, _P], _I32),
+    "tr_batched_plan_describe": ([_P], ctypes.c_char_p),
+    "tr_batched_plan_destroy": ([_P], _I32),
 }
 
 
@@ -204,3 +209,41 @@ def tr_scan_noalloc(m: dict, x: torch.Tensor, y: torch.Tensor, status: torch.Ten
     s = (stream or torch.cuda.current_stream()).cuda_stream
     _check(lib().tr_scan_noalloc(md.ref(), _ptr(x), dtype_of(x), _ptr(y), dtype_of(y), x.numel(), _ptr(carry_in),
                                  _ptr(status), s))
+
+
+class BatchPlan:
+    """A tr_batched plan over a list of f32 device tensors, one map dict each."""
+
+    def __init__(self, xs, maps, sums, mins, maxs, ops: int = TR_SUM | TR_MIN | TR_MAX, autotune: bool = False,
+                 stream=None):
+        n = len(xs)
+        self._keep = [MapDesc(m) for m in maps]
+        descs = (tr_map_desc * n)(*[d.c for d in self._keep])
+        ptrs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        lens = (ctypes.c_int64 * n)(*[x.numel() for x in xs])
+        self._refs = (xs, sums, mins, maxs)
+        self.handle = ctypes.c_void_p()
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        _check(lib().tr_batched_plan_create(n, ptrs, lens, descs, ops, _ptr(sums), _ptr(mins), _ptr(maxs),
+                                            int(autotune), s, ctypes.byref(self.handle)))
+
+    def describe(self) -> str:
+        return lib().tr_batched_plan_describe(self.handle).decode()
+
+    def run(self, stream=None) -> None:
+        _check(lib().tr_batched_run(self.handle, (stream or torch.cuda.current_stream()).cuda_stream))
+
+    def run_unbatched(self, use_graph: bool = False, stream=None) -> None:
+        _check(lib().tr_batched_run_unbatched(self.handle, int(use_graph),
+                                              (stream or torch.cuda.current_stream()).cuda_stream))
+
+    def close(self) -> None:
+        if self.handle:
+            lib().tr_batched_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

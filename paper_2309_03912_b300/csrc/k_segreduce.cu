@@ -6,7 +6,7 @@
 // then walks the segments in order, keeping a window of 32 offsets in
 // registers (one per lane).  Each segment piece -- the intersection of a
 // segment with the range -- is reduced by the whole warp: 128-bit loads,
-// kUnroll vectors in flight per lane, the map in registers, Kahan-compensated
+// kRangeUnroll vectors in flight per lane, the map in registers, Kahan-compensated
 // per-lane sums of pairwise vector sums, then a float-float warp butterfly.
 //   * a piece that is the whole segment is written out directly;
 //   * a piece cut by the range start (head) or end (tail) goes to a per-warp
@@ -17,6 +17,7 @@
 // reported through the workspace status word instead of faulting.
 #include "accum.cuh"
 #include "dispatch.cuh"
+#include "range.cuh"
 
 namespace tr {
 
@@ -24,7 +25,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kUnroll = 4;
 constexpr int kMaxGrid = 2048;
 
 struct SegSlot {
@@ -55,45 +55,6 @@ __device__ __forceinline__ int64_t warp_lower_bound(const int64_t* off, int64_t 
   const bool ge = p < hi ? (__ldg(off + p) >= a) : true;
   const unsigned mask = __ballot_sync(kFull, ge);
   return lo + (mask ? __ffs(mask) - 1 : 0);
-}
-
-template <class In, class F>
-__device__ __forceinline__ Acc<float> reduce_piece(const In* __restrict__ x, int64_t pa, int64_t pb, int x_aligned,
-                                                   const F& f, int lane) {
-  using S = Storage<In>;
-  constexpr int V = S::kVec;
-  Acc<float> acc;
-  if (pa >= pb) return acc;
-  const int64_t va = (pa + V - 1) / V, vb = pb / V;
-  if (!x_aligned || va >= vb) {  // misaligned base, or under two vectors' worth: element-wise
-    for (int64_t i = pa + lane; i < pb; i += 32) acc.add(f(S::cvt(x[i])));
-    return acc;
-  }
-  if (pa + lane < va * V) acc.add(f(S::cvt(x[pa + lane])));      // head (< V elements)
-  if (vb * V + lane < pb) acc.add(f(S::cvt(x[vb * V + lane])));  // tail (< V elements)
-  const uint4* xv = reinterpret_cast<const uint4*>(x);
-  int64_t v = va + lane;
-  for (; v + 32 * (kUnroll - 1) < vb; v += 32 * kUnroll) {
-    uint4 raw[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) raw[u] = ld_stream(xv + v + 32 * u);
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      float e[V];
-      S::unpack(raw[u], e);
-#pragma unroll
-      for (int i = 0; i < V; ++i) e[i] = f(e[i]);
-      acc.template add_vec<V>(e);
-    }
-  }
-  for (; v < vb; v += 32) {
-    float e[V];
-    S::unpack(ld_stream(xv + v), e);
-#pragma unroll
-    for (int i = 0; i < V; ++i) e[i] = f(e[i]);
-    acc.template add_vec<V>(e);
-  }
-  return acc;
 }
 
 __device__ __forceinline__ void write_slot(SegSlot* sl, long long seg, const Acc<float>::W& w, int through) {
@@ -138,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
         break;
       }
       const int64_t pa = imax(lo_s, a), pb = imin(hi_s, b);
-      const Acc<float> acc = reduce_piece<In, F>(x, pa, pb, x_aligned, f, lane);
+      const Acc<float> acc = warp_reduce_range<In, F>(x, pa, pb, x_aligned, f, lane);
       const Acc<float>::W w = acc.warp();
       const bool head_open = lo_s < a, tail_open = hi_s > b;
       if (lane == 0) {

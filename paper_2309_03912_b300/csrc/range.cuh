@@ -1,0 +1,53 @@
+// range.cuh -- one warp reduces f over the elements [pa, pb) of an array:
+// 128-bit loads with kRangeUnroll vectors in flight per lane, a scalar head
+// and tail around the 16-byte-aligned body, the map in registers, and the
+// per-lane Kahan-compensated accumulator of accum.cuh.  Every lane returns
+// its own accumulator; combine with Acc<float>::warp().
+#pragma once
+
+#include "accum.cuh"
+
+namespace tr {
+
+constexpr int kRangeUnroll = 4;
+
+template <class In, class F>
+__device__ __forceinline__ Acc<float> warp_reduce_range(const In* __restrict__ x, int64_t pa, int64_t pb, int x_aligned,
+                                                   const F& f, int lane) {
+  using S = Storage<In>;
+  constexpr int V = S::kVec;
+  Acc<float> acc;
+  if (pa >= pb) return acc;
+  const int64_t va = (pa + V - 1) / V, vb = pb / V;
+  if (!x_aligned || va >= vb) {  // misaligned base, or under two vectors' worth: element-wise
+    for (int64_t i = pa + lane; i < pb; i += 32) acc.add(f(S::cvt(x[i])));
+    return acc;
+  }
+  if (pa + lane < va * V) acc.add(f(S::cvt(x[pa + lane])));      // head (< V elements)
+  if (vb * V + lane < pb) acc.add(f(S::cvt(x[vb * V + lane])));  // tail (< V elements)
+  const uint4* xv = reinterpret_cast<const uint4*>(x);
+  int64_t v = va + lane;
+  for (; v + 32 * (kRangeUnroll - 1) < vb; v += 32 * kRangeUnroll) {
+    uint4 raw[kRangeUnroll];
+#pragma unroll
+    for (int u = 0; u < kRangeUnroll; ++u) raw[u] = ld_stream(xv + v + 32 * u);
+#pragma unroll
+    for (int u = 0; u < kRangeUnroll; ++u) {
+      float e[V];
+      S::unpack(raw[u], e);
+#pragma unroll
+      for (int i = 0; i < V; ++i) e[i] = f(e[i]);
+      acc.template add_vec<V>(e);
+    }
+  }
+  for (; v < vb; v += 32) {
+    float e[V];
+    S::unpack(ld_stream(xv + v), e);
+#pragma unroll
+    for (int i = 0; i < V; ++i) e[i] = f(e[i]);
+    acc.template add_vec<V>(e);
+  }
+  return acc;
+}
+
+}  // namespace tr
