@@ -57,6 +57,10 @@ def parse():
     p.add_argument("--impl", default="tr", choices=["tr", "reference"])
     p.add_argument("--no-configs", action="store_true", help="headline only")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    p.add_argument("--only", default="", help="comma-separated names of the extra configurations to run "
+                                              "(scan_u32, scan_f32, reduce_f64, mixers_2^20, batched, f16); "
+                                              "skips the headline")
+    p.add_argument("--config-log2", type=int, default=28, help="log2 size of the 2^28 scan configurations")
     p.add_argument("--head-n", type=int, default=N_HEAD,
                    help="elements of the headline workload (segments scale with it); smaller sizes are "
                         "for profiler captures only")
@@ -280,6 +284,9 @@ def other_configs(args, stream, hbm_peak):
 
     out = {}
     steps, warm = max(5, min(args.steps, 20)), 3
+    only = [o for o in args.only.split(",") if o]
+    want = lambda name: not only or name in only
+    big = 1 << args.config_log2
 
     def record(name, ms, n, nbytes, launches, extra=None):
         gbs = nbytes / (ms * 1e-3) / 1e9
@@ -291,103 +298,109 @@ def other_configs(args, stream, hbm_peak):
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2, for the L2-resident sizes
 
-    # plain FP64 Horner reduce, N = 2^20 (L2-resident: timed as graph replays of 20 calls,
-    # with and without an L2 flush before each call)
-    x, m = I.horner_f64(1 << 20)
-    xd = torch.from_numpy(x).cuda()
-    ws = B.workspace(B.tr_reduce_workspace_size(x.size, B.TR_F64))
-    s = torch.empty(3, dtype=torch.float64, device="cuda")
-    f = lambda: B.tr_reduce(m, xd, 7, s[0:1], s[1:2], s[2:3], B.make_exec(ws))
-    ms = time_graph(f, 20, stream)
-    ms_flush = time_graph(lambda: (flush.zero_(), f()), 20, stream) - time_graph(lambda: flush.zero_(), 20, stream)
-    record("reduce_f64_horner8_2^20", ms, x.size, x.nbytes, 1,
-           {"ms_after_l2_flush": round(ms_flush, 5), "timing": "cuda graph of 20 calls",
-            "bound": "FP64 ALU (B300 FP64 is ~1/64 of FP32) and launch latency"})
+    if want('reduce_f64'):
+        # plain FP64 Horner reduce, N = 2^20 (L2-resident: timed as graph replays of 20 calls,
+        # with and without an L2 flush before each call)
+        x, m = I.horner_f64(1 << 20)
+        xd = torch.from_numpy(x).cuda()
+        ws = B.workspace(B.tr_reduce_workspace_size(x.size, B.TR_F64))
+        s = torch.empty(3, dtype=torch.float64, device="cuda")
+        f = lambda: B.tr_reduce(m, xd, 7, s[0:1], s[1:2], s[2:3], B.make_exec(ws))
+        ms = time_graph(f, 20, stream)
+        ms_flush = time_graph(lambda: (flush.zero_(), f()), 20, stream) - time_graph(lambda: flush.zero_(), 20, stream)
+        record("reduce_f64_horner8_2^20", ms, x.size, x.nbytes, 1,
+               {"ms_after_l2_flush": round(ms_flush, 5), "timing": "cuda graph of 20 calls",
+                "bound": "FP64 ALU (B300 FP64 is ~1/64 of FP32) and launch latency"})
 
-    # u32 xorshift32: exact u64 sum + u32 -> u64 inclusive scan, N = 2^20
-    xu = I.mixer_u32(1 << 20)
-    xud = torch.from_numpy(xu.view(np.int32)).cuda()
-    wsr = B.workspace(B.tr_reduce_workspace_size(xu.size, B.TR_U32))
-    wss = B.workspace(B.tr_scan_workspace_size(xu.size, B.TR_U32, B.TR_U64))
-    s64 = torch.empty(1, dtype=torch.int64, device="cuda")
-    y64 = torch.empty(xu.size, dtype=torch.int64, device="cuda")
+    if want('mixers_2^20'):
+        # u32 xorshift32: exact u64 sum + u32 -> u64 inclusive scan, N = 2^20
+        xu = I.mixer_u32(1 << 20)
+        xud = torch.from_numpy(xu.view(np.int32)).cuda()
+        wsr = B.workspace(B.tr_reduce_workspace_size(xu.size, B.TR_U32))
+        wss = B.workspace(B.tr_scan_workspace_size(xu.size, B.TR_U32, B.TR_U64))
+        s64 = torch.empty(1, dtype=torch.int64, device="cuda")
+        y64 = torch.empty(xu.size, dtype=torch.int64, device="cuda")
 
-    def c1b():
-        B.tr_reduce({"kind": "xorshift32"}, xud, 1, s64, None, None, B.make_exec(wsr))
-        B.tr_scan({"kind": "xorshift32"}, xud, y64, B.make_exec(wss))
-    ms = time_graph(c1b, 20, stream)
-    record("sum_u64_and_scan_u64_xorshift32_2^20", ms, xu.size, xu.nbytes * 2 + y64.numel() * 8, 2,
-           {"timing": "cuda graph of 20 calls"})
-    del xud, y64
+        def c1b():
+            B.tr_reduce({"kind": "xorshift32"}, xud, 1, s64, None, None, B.make_exec(wsr))
+            B.tr_scan({"kind": "xorshift32"}, xud, y64, B.make_exec(wss))
+        ms = time_graph(c1b, 20, stream)
+        record("sum_u64_and_scan_u64_xorshift32_2^20", ms, xu.size, xu.nbytes * 2 + y64.numel() * 8, 2,
+               {"timing": "cuda graph of 20 calls"})
+        del xud, y64
 
-    # u32 splitmix32 inclusive scan mod 2^32, N = 2^28
-    xu = I.mixer_u32(1 << 28, stream="mixer_u32_scan")
-    xud = torch.from_numpy(xu.view(np.int32)).cuda()
-    del xu
-    y = torch.empty_like(xud)
-    wss = B.workspace(B.tr_scan_workspace_size(xud.numel(), B.TR_U32, B.TR_U32))
-    exs = B.make_exec(wss, stream=stream)
-    ms, _, _ = time_launches(lambda: B.tr_scan({"kind": "splitmix32"}, xud, y, exs), steps, warm, stream)
-    record("scan_u32_splitmix32_2^28", ms, xud.numel(), xud.numel() * 8, 1)
-    del xud, y
+    if want('scan_u32'):
+        # u32 splitmix32 inclusive scan mod 2^32, N = 2^28
+        xu = I.mixer_u32(big, stream="mixer_u32_scan")
+        xud = torch.from_numpy(xu.view(np.int32)).cuda()
+        del xu
+        y = torch.empty_like(xud)
+        wss = B.workspace(B.tr_scan_workspace_size(xud.numel(), B.TR_U32, B.TR_U32))
+        exs = B.make_exec(wss, stream=stream)
+        ms, _, _ = time_launches(lambda: B.tr_scan({"kind": "splitmix32"}, xud, y, exs), steps, warm, stream)
+        record("scan_u32_splitmix32_2^28", ms, xud.numel(), xud.numel() * 8, 1)
+        del xud, y
 
-    # f32 compensated scan of x^2, N = 2^28
-    xf = I.square_f32(1 << 28)
-    xfd = torch.from_numpy(xf).cuda()
-    del xf
-    y = torch.empty_like(xfd)
-    wss = B.workspace(B.tr_scan_workspace_size(xfd.numel(), B.TR_F32, B.TR_F32))
-    exs = B.make_exec(wss, stream=stream)
-    ms, _, _ = time_launches(lambda: B.tr_scan(I.simple_map("square"), xfd, y, exs), steps, warm, stream)
-    record("scan_f32_square_compensated_2^28", ms, xfd.numel(), xfd.numel() * 8, 1)
-    del xfd, y
+    if want('scan_f32'):
+        # f32 compensated scan of x^2, N = 2^28
+        xf = I.square_f32(big)
+        xfd = torch.from_numpy(xf).cuda()
+        del xf
+        y = torch.empty_like(xfd)
+        wss = B.workspace(B.tr_scan_workspace_size(xfd.numel(), B.TR_F32, B.TR_F32))
+        exs = B.make_exec(wss, stream=stream)
+        ms, _, _ = time_launches(lambda: B.tr_scan(I.simple_map("square"), xfd, y, exs), steps, warm, stream)
+        record("scan_f32_square_compensated_2^28", ms, xfd.numel(), xfd.numel() * 8, 1)
+        del xfd, y
 
-    # batched: 10,000 f32 arrays (separate allocations), lengths log-uniform in [1, 2^20], map per array from
-    # {Horner deg 4-16, rational 6/6, Newton 6}; one persistent launch in a CUDA graph, autotuned tiles,
-    # against one tr_reduce launch per array (eager, and the same launches recorded in a graph)
-    xs, lens, maps = I.batched(10000)
-    total = int(np.sum(lens))
-    dev = [torch.from_numpy(x).cuda() for x in xs]
-    del xs
-    nb = len(dev)
-    bs = torch.zeros(nb, dtype=torch.float64, device="cuda")
-    bmn = torch.zeros(nb, dtype=torch.float32, device="cuda")
-    bmx = torch.zeros(nb, dtype=torch.float32, device="cuda")
-    with torch.cuda.stream(stream):
-        plan = B.BatchPlan(dev, maps, bs, bmn, bmx, autotune=True, stream=stream)
-    ms_b, _, _ = time_launches(lambda: plan.run(stream), steps, warm, stream)
-    ms_eager, _, _ = time_launches(lambda: plan.run_unbatched(False, stream), 3, 1, stream)
-    ms_graph, _, _ = time_launches(lambda: plan.run_unbatched(True, stream), 3, 1, stream)
-    kinds = {}
-    for m in maps:
-        kinds[m["kind"]] = kinds.get(m["kind"], 0) + 1
-    record("batched_10000_arrays_mixed_maps", ms_b, total, total * 4, 1,
-           {"plan": plan.describe(), "arrays": nb, "maps": kinds, "unbatched_eager_ms": round(ms_eager, 4),
-            "unbatched_graph_ms": round(ms_graph, 4), "speedup_vs_eager": round(ms_eager / ms_b, 2),
-            "speedup_vs_graph": round(ms_graph / ms_b, 2), "launches_unbatched": nb})
-    plan.close()
-    del dev
+    if want('batched'):
+        # batched: 10,000 f32 arrays (separate allocations), lengths log-uniform in [1, 2^20], map per array from
+        # {Horner deg 4-16, rational 6/6, Newton 6}; one persistent launch in a CUDA graph, autotuned tiles,
+        # against one tr_reduce launch per array (eager, and the same launches recorded in a graph)
+        xs, lens, maps = I.batched(10000)
+        total = int(np.sum(lens))
+        dev = [torch.from_numpy(x).cuda() for x in xs]
+        del xs
+        nb = len(dev)
+        bs = torch.zeros(nb, dtype=torch.float64, device="cuda")
+        bmn = torch.zeros(nb, dtype=torch.float32, device="cuda")
+        bmx = torch.zeros(nb, dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(stream):
+            plan = B.BatchPlan(dev, maps, bs, bmn, bmx, autotune=True, stream=stream)
+        ms_b, _, _ = time_launches(lambda: plan.run(stream), steps, warm, stream)
+        ms_eager, _, _ = time_launches(lambda: plan.run_unbatched(False, stream), 3, 1, stream)
+        ms_graph, _, _ = time_launches(lambda: plan.run_unbatched(True, stream), 3, 1, stream)
+        kinds = {}
+        for m in maps:
+            kinds[m["kind"]] = kinds.get(m["kind"], 0) + 1
+        record("batched_10000_arrays_mixed_maps", ms_b, total, total * 4, 1,
+               {"plan": plan.describe(), "arrays": nb, "maps": kinds, "unbatched_eager_ms": round(ms_eager, 4),
+                "unbatched_graph_ms": round(ms_graph, 4), "speedup_vs_eager": round(ms_eager / ms_b, 2),
+                "speedup_vs_graph": round(ms_graph / ms_b, 2), "launches_unbatched": nb})
+        plan.close()
+        del dev
 
-    # FP16 storage, FP32 compute: Horner deg 8 sum/min/max, N = 2^30
-    xh, m = I.horner_f16(1 << 30)
-    xhd = torch.from_numpy(xh).cuda()
-    del xh
-    ws = B.workspace(B.tr_reduce_workspace_size(xhd.numel(), B.TR_F16))
-    ex = B.make_exec(ws, stream=stream)
-    s = torch.empty(1, dtype=torch.float64, device="cuda")
-    mm = torch.empty(2, dtype=torch.float32, device="cuda")
-    ms16, _, _ = time_launches(lambda: B.tr_reduce(m, xhd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
-    record("reduce_f16_storage_horner8_2^30", ms16, xhd.numel(), xhd.numel() * 2, 1)
-    # the same values in f32 storage: the plain FP32 comparison for the mixed-precision form
-    xfd = xhd.float()
-    del xhd
-    ws = B.workspace(B.tr_reduce_workspace_size(xfd.numel(), B.TR_F32))
-    ex = B.make_exec(ws, stream=stream)
-    ms32, _, _ = time_launches(lambda: B.tr_reduce(m, xfd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
-    record("reduce_f32_storage_horner8_2^30", ms32, xfd.numel(), xfd.numel() * 4, 1,
-           {"f16_storage_speedup": round(ms32 / ms16, 3)})
-    del xfd
-    B.tr_check(ex)
+    if want('f16'):
+        # FP16 storage, FP32 compute: Horner deg 8 sum/min/max, N = 2^30
+        xh, m = I.horner_f16(1 << 30)
+        xhd = torch.from_numpy(xh).cuda()
+        del xh
+        ws = B.workspace(B.tr_reduce_workspace_size(xhd.numel(), B.TR_F16))
+        ex = B.make_exec(ws, stream=stream)
+        s = torch.empty(1, dtype=torch.float64, device="cuda")
+        mm = torch.empty(2, dtype=torch.float32, device="cuda")
+        ms16, _, _ = time_launches(lambda: B.tr_reduce(m, xhd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
+        record("reduce_f16_storage_horner8_2^30", ms16, xhd.numel(), xhd.numel() * 2, 1)
+        # the same values in f32 storage: the plain FP32 comparison for the mixed-precision form
+        xfd = xhd.float()
+        del xhd
+        ws = B.workspace(B.tr_reduce_workspace_size(xfd.numel(), B.TR_F32))
+        ex = B.make_exec(ws, stream=stream)
+        ms32, _, _ = time_launches(lambda: B.tr_reduce(m, xfd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
+        record("reduce_f32_storage_horner8_2^30", ms32, xfd.numel(), xfd.numel() * 4, 1,
+               {"f16_storage_speedup": round(ms32 / ms16, 3)})
+        del xfd
+
     torch.cuda.synchronize()
     return out
 
@@ -459,6 +472,9 @@ def main():
     hbm_peak, _, peak_src = peaks()
     stream = torch.cuda.Stream()
 
+    if args.only:
+        print(json.dumps({"configs": other_configs(args, stream, hbm_peak)}))
+        return 0
     h = headline(args, rank, world, stream)
     configs = None if (args.no_configs or rank != 0) else other_configs(args, stream, hbm_peak)
     cb = oracle_sample()[0] if (rank == 0 and world == 1 and not args.no_cpu) else None
