@@ -12,6 +12,7 @@
  *     the same per segment [off[s], off[s+1])    tr_segmented_reduce
  *     inclusive prefix sums of f                 tr_scan
  *     thousands of arrays, mixed maps, one graph tr_batched_*
+ *     many polynomials at many points (GEMM)     tr_vandermonde
  *
  * Conventions (all entry points):
  *   - Every pointer named d_* or documented "device" is CUDA device memory
@@ -223,6 +224,29 @@ tr_status tr_batched_run_unbatched(tr_batch_plan* plan, int use_graph, void* str
 const char* tr_batched_plan_describe(const tr_batch_plan* plan);
 
 tr_status tr_batched_plan_destroy(tr_batch_plan* plan);
+
+/* ---- dense Vandermonde product ---------------------------------------------- */
+
+enum { TR_PREC_BF16X3 = 0, TR_PREC_FP32 = 1 };
+
+/* Workspace of tr_vandermonde (a status header; 256 bytes). */
+tr_status tr_vandermonde_workspace_size(size_t* bytes);
+
+/* Many polynomials at many points: Y = V(x) C, Y[i][j] = sum_k C[k][j] x_i^k.
+ *   d_x     m FP32 points;  d_coef (deg+1) x npoly FP32, row-major, row k
+ *           holding the power-k coefficients of all polynomials (deg <= 31);
+ *   d_y     m x npoly FP32, row-major.
+ * TR_PREC_BF16X3: split-BF16 on the tcgen05 tensor cores (Henry, Tang &
+ *   Heinecke, ARITH 2019): V = Vh + Vl, C = Ch + Cl, Y ~= Vh Ch + Vh Cl + Vl Ch
+ *   accumulated in FP32 in tensor memory; V is generated on the fly from x.
+ *   Needs m % 128 == 0, npoly % 256 == 0, a 16-byte aligned d_y and a
+ *   workspace of tr_vandermonde_workspace_size() bytes (its status word
+ *   reports a device-side timeout through tr_check).  Error, normwise against
+ *   S[i][j] = sum_k |C[k][j]| |x_i|^k: about 1e-5.
+ * TR_PREC_FP32: FP32 Horner with fma on the CUDA cores, any m and npoly.
+ * Rows beyond deg are treated as zero coefficients. */
+tr_status tr_vandermonde(const float* d_x, int64_t m, const float* d_coef, int32_t deg, int64_t npoly,
+                         int precision, float* d_y, const tr_exec* exec);
 
 /* ---- inclusive scan without a workspace -------------------------------------- */
 

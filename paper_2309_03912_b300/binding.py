@@ -76,6 +76,8 @@ SIGNATURES = {
     "tr_batched_run_unbatched": ([_P, _I32, _P], _I32),
     "tr_batched_plan_describe": ([_P], ctypes.c_char_p),
     "tr_batched_plan_destroy": ([_P], _I32),
+    "tr_vandermonde_workspace_size": ([ctypes.POINTER(_SZ)], _I32),
+    "tr_vandermonde": ([_P, _I64, _P, _I32, _I64, _I32, _P, _E], _I32),
 }
 
 
@@ -247,3 +249,9 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def tr_vandermonde(x: torch.Tensor, coef: torch.Tensor, y: torch.Tensor, precision: int, ex: tr_exec) -> None:
+    """Y = V(x) C: x (m,) f32, coef (deg+1, npoly) f32 row-major, y (m, npoly) f32."""
+    _check(lib().tr_vandermonde(_ptr(x), x.numel(), _ptr(coef), coef.shape[0] - 1, coef.shape[1], precision, _ptr(y),
+                                ctypes.byref(ex)))
