@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--no-configs", action="store_true", help="headline only")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     p.add_argument("--only", default="", help="comma-separated names of the extra configurations to run "
-                                              "(scan_u32, scan_f32, reduce_f64, mixers_2^20, batched, f16); "
+                                              "(scan_u32, scan_f32, reduce_f64, mixers_2^20, batched, vandermonde, f16); "
                                               "skips the headline")
     p.add_argument("--config-log2", type=int, default=28, help="log2 size of the 2^28 scan configurations")
     p.add_argument("--head-n", type=int, default=N_HEAD,
@@ -379,6 +379,29 @@ def other_configs(args, stream, hbm_peak):
                 "speedup_vs_graph": round(ms_graph / ms_b, 2), "launches_unbatched": nb})
         plan.close()
         del dev
+
+    if want('vandermonde'):
+        # 4096 polynomials of degree 31 at 2^20 points: Y = V(x) C (16 GiB of FP32 output), split-BF16 on
+        # the tensor cores against plain FP32 Horner on the CUDA cores
+        x, C = I.vandermonde()
+        xd, Cd = torch.from_numpy(x).cuda(), torch.from_numpy(C).cuda()
+        m, npoly = x.size, C.shape[1]
+        y = torch.empty((m, npoly), dtype=torch.float32, device="cuda")
+        wsv = B.workspace(256)
+        exv = B.make_exec(wsv, stream=stream)
+        vs = max(3, steps // 4)
+        ms_tc, _, _ = time_launches(lambda: B.tr_vandermonde(xd, Cd, y, B.TR_PREC_BF16X3, exv), vs, 2, stream)
+        ms_32, _, _ = time_launches(lambda: B.tr_vandermonde(xd, Cd, y, B.TR_PREC_FP32, exv), vs, 2, stream)
+        B.tr_check(exv)
+        flops = 2.0 * m * 32 * npoly
+        nbytes = m * npoly * 4 + m * 4 + C.nbytes
+        record("vandermonde_bf16x3_2^20x32x4096", ms_tc, m * npoly, nbytes, 1,
+               {"bound": "hbm (output write)", "tflops_algorithmic": round(flops / (ms_tc * 1e-3) / 1e12, 1),
+                "tflops_tensor_executed": round(3 * flops / (ms_tc * 1e-3) / 1e12, 1),
+                "fp32_horner_ms": round(ms_32, 4), "speedup_vs_fp32_horner": round(ms_32 / ms_tc, 3)})
+        record("vandermonde_fp32_horner_2^20x32x4096", ms_32, m * npoly, nbytes, 1,
+               {"bound": "fp32 fma pipe / hbm", "tflops": round(flops / (ms_32 * 1e-3) / 1e12, 1)})
+        del y, xd, Cd
 
     if want('f16'):
         # FP16 storage, FP32 compute: Horner deg 8 sum/min/max, N = 2^30
