@@ -42,8 +42,7 @@ __global__ void __launch_bounds__(kThreads) k_map(const In* __restrict__ x, type
         if (vi < nvec) {
           C v[V];
           S::unpack(raw[u], v);
-#pragma unroll
-          for (int i = 0; i < V; ++i) v[i] = f(v[i]);
+          map_vec<V>(f, v);
 #pragma unroll
           for (int j = 0; j < kOut16; ++j) st_stream(yv + vi * kOut16 + j, pack16(v + j * (16 / (int)sizeof(C))));
         }

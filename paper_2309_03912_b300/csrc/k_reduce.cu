@@ -47,8 +47,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const In* __restrict__ x, i
       for (int u = 0; u < kUnroll; ++u) {
         C v[V];
         S::unpack(raw[u], v);
-#pragma unroll
-        for (int i = 0; i < V; ++i) v[i] = f(v[i]);
+        map_vec<V>(f, v);
         acc.template add_vec<V>(v);
       }
     } else {
@@ -57,8 +56,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const In* __restrict__ x, i
         if (vi < nvec) {
           C v[V];
           S::unpack(ld_stream(xv + vi), v);
-#pragma unroll
-          for (int i = 0; i < V; ++i) v[i] = f(v[i]);
+          map_vec<V>(f, v);
           acc.template add_vec<V>(v);
         }
       }

@@ -141,8 +141,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const In* __restrict__ x, typ
     for (int j = 0; j < kLoads; ++j) raw[j] = ld_cached(xv + j);
 #pragma unroll
     for (int j = 0; j < kLoads; ++j) S::unpack(raw[j], v + j * V);
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) v[i] = f(v[i]);
+    map_vec<kItems>(f, v);
   } else {
 #pragma unroll
     for (int i = 0; i < kItems; ++i) v[i] = (base + i < n) ? f(S::cvt(x[base + i])) : C(0);

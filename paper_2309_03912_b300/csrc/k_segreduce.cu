@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
         break;
       }
       const int64_t pa = imax(lo_s, a), pb = imin(hi_s, b);
-      const Acc<float> acc = warp_reduce_range<In, F>(x, pa, pb, x_aligned, f, lane);
+      const Acc<float> acc = warp_reduce_range<In, F>(x, pa, pb, x_aligned, f, lane, b);
       const Acc<float>::W w = acc.warp();
       const bool head_open = lo_s < a, tail_open = hi_s > b;
       if (lane == 0) {

@@ -23,6 +23,56 @@
 
 namespace tr {
 
+// Two maps at once.  On the device, FP32 Horner steps of two points run as one
+// packed instruction (fma.rn.f32x2: each half is an IEEE fma, so results are
+// bit-identical to two scalar fmas); elsewhere the scalar form is used.  The
+// signature is the same in every pass (the paper's Sec. 2.4 rule); only the
+// body differs.
+#if defined(__CUDA_ARCH__)
+__device__ __forceinline__ unsigned long long pack_f32x2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack_f32x2(unsigned long long r, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a, unsigned long long b,
+                                                         unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+#endif
+
+// Horner on two points with the same coefficients: (p0, p1) = (P(x0), P(x1)).
+template <class T, int D>
+TR_HD inline void horner_pair(const T* c, T x0, T x1, T& p0, T& p1) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (std::is_same<T, float>::value) {
+    const unsigned long long xx = pack_f32x2(x0, x1);
+    unsigned long long p = pack_f32x2(c[D], c[D]);
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) p = fma_f32x2(p, xx, pack_f32x2(c[k], c[k]));
+    unpack_f32x2(p, p0, p1);
+    return;
+  }
+#endif
+  p0 = c[D];
+  p1 = c[D];
+  for (int k = D - 1; k >= 0; --k) {
+    p0 = fma_hd(p0, x0, c[k]);
+    p1 = fma_hd(p1, x1, c[k]);
+  }
+}
+
+// Trait: does map F provide eval2 (two points per call)?  Member detection in
+// the manner of the paper's has_xxx helper (Sec. 4).
+template <class F, class = void>
+struct has_eval2 : std::false_type {};
+template <class F>
+struct has_eval2<F, std::void_t<decltype(&F::eval2)>> : std::true_type {};
+
 template <class T>
 struct Identity {
   static constexpr HDC hdc = HDC::HstDev;
@@ -54,6 +104,7 @@ struct Horner {
     for (int k = D - 1; k >= 0; --k) p = fma_hd(p, x, c[k]);
     return p;
   }
+  TR_HD void eval2(T x0, T x1, T& y0, T& y1) const { horner_pair<T, D>(c, x0, x1, y0, y1); }
 };
 
 // Run-time degree: coefficients by pointer.
@@ -78,6 +129,13 @@ struct Rational {
 #pragma unroll
     for (int k = DQ - 1; k >= 0; --k) b = fma_hd(b, x, q[k]);
     return a / b;
+  }
+  TR_HD void eval2(T x0, T x1, T& y0, T& y1) const {
+    T a0, a1, b0, b1;
+    horner_pair<T, DP>(p, x0, x1, a0, a1);
+    horner_pair<T, DQ>(q, x0, x1, b0, b1);
+    y0 = a0 / b0;
+    y1 = a1 / b1;
   }
 };
 

@@ -2,7 +2,9 @@
 // 128-bit loads with kRangeUnroll vectors in flight per lane, a scalar head
 // and tail around the 16-byte-aligned body, the map in registers, and the
 // per-lane Kahan-compensated accumulator of accum.cuh.  Every lane returns
-// its own accumulator; combine with Acc<float>::warp().
+// its own accumulator; combine with Acc<float>::warp().  While it streams,
+// lane 0 asks L2 for the data kPrefetchAhead chunks ahead (up to element
+// pf_limit, the end of the region this warp will read).
 #pragma once
 
 #include "accum.cuh"
@@ -10,10 +12,12 @@
 namespace tr {
 
 constexpr int kRangeUnroll = 4;
+// Chunks (32 lanes x kRangeUnroll vectors) requested into L2 ahead of use.
+constexpr int kPrefetchAhead = 4;
 
 template <class In, class F>
 __device__ __forceinline__ Acc<float> warp_reduce_range(const In* __restrict__ x, int64_t pa, int64_t pb, int x_aligned,
-                                                   const F& f, int lane) {
+                                                        const F& f, int lane, int64_t pf_limit) {
   using S = Storage<In>;
   constexpr int V = S::kVec;
   Acc<float> acc;
@@ -27,7 +31,12 @@ __device__ __forceinline__ Acc<float> warp_reduce_range(const In* __restrict__ x
   if (vb * V + lane < pb) acc.add(f(S::cvt(x[vb * V + lane])));  // tail (< V elements)
   const uint4* xv = reinterpret_cast<const uint4*>(x);
   int64_t v = va + lane;
+  const int64_t vpf_end = pf_limit / V;  // prefetches stay below element pf_limit
   for (; v + 32 * (kRangeUnroll - 1) < vb; v += 32 * kRangeUnroll) {
+    if (lane == 0) {
+      const int64_t pv = v + (int64_t)kPrefetchAhead * 32 * kRangeUnroll;
+      if (pv + 32 * kRangeUnroll <= vpf_end) prefetch_l2(xv + pv, 32 * kRangeUnroll * 16);
+    }
     uint4 raw[kRangeUnroll];
 #pragma unroll
     for (int u = 0; u < kRangeUnroll; ++u) raw[u] = ld_stream(xv + v + 32 * u);
@@ -35,16 +44,14 @@ __device__ __forceinline__ Acc<float> warp_reduce_range(const In* __restrict__ x
     for (int u = 0; u < kRangeUnroll; ++u) {
       float e[V];
       S::unpack(raw[u], e);
-#pragma unroll
-      for (int i = 0; i < V; ++i) e[i] = f(e[i]);
+      map_vec<V>(f, e);
       acc.template add_vec<V>(e);
     }
   }
   for (; v < vb; v += 32) {
     float e[V];
     S::unpack(ld_stream(xv + v), e);
-#pragma unroll
-    for (int i = 0; i < V; ++i) e[i] = f(e[i]);
+    map_vec<V>(f, e);
     acc.template add_vec<V>(e);
   }
   return acc;
