@@ -4,12 +4,15 @@
 // parallel prefix scan with decoupled look-back", NVR-2016-002):
 //   * each block takes a tile id from an atomic counter (dynamic ids: every
 //     tile's predecessors have already started, so waiting on them ends);
-//   * a thread owns kItems contiguous elements (128-bit loads), scans them
-//     serially, then warps scan lane totals with shuffles and the block scans
-//     warp totals in shared memory;
-//   * the tile publishes its aggregate (flag A), warp 0 looks back over up to
-//     32 predecessors at a time, summing aggregates until it meets an
-//     inclusive prefix (flag P), then publishes its own inclusive prefix;
+//   * a thread owns kItems contiguous elements (128-bit loads) and keeps only
+//     the mapped values in registers; warps scan lane totals with shuffles and
+//     the block combines warp totals in shared memory;
+//   * the tile publishes its aggregate (flag A), then the whole block looks
+//     back over kThreads predecessors per round (one flag per thread), summing
+//     aggregates until it meets an inclusive prefix (flag P), and publishes its
+//     own inclusive prefix.  With hundreds of tiles in flight the nearest P is
+//     usually several hundred tiles back, so a block-wide window takes one or
+//     two rounds where a single warp would need tens;
 //   * every wait is bounded by a %globaltimer deadline and an abort word: on
 //     expiry the block records TR_ERR_TIMEOUT and finishes instead of hanging.
 // Tile flags carry a 30-bit call epoch, so no per-call reset is needed: the
@@ -28,8 +31,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;  // 4096 elements
+constexpr int kItems = 32;
+constexpr int kTile = kThreads * kItems;  // 8192 elements
 
 constexpr uint32_t kFlagA = 1, kFlagP = 2;
 
@@ -110,10 +113,12 @@ __global__ void __launch_bounds__(kThreads) k_scan(const In* __restrict__ x, typ
 
   __shared__ uint32_t s_tile, s_tag;
   __shared__ T s_warp[kWarps];
+  __shared__ Carry s_red[kWarps];
+  __shared__ int s_first[kWarps];
   __shared__ Carry s_prefix;
 
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) {
     const uint32_t ep = ld_relaxed_u32(&hdr->epoch);
     const uint32_t t = atom_add_acq_rel_u32(&hdr->tile_counter, 1u);
     if (t == gridDim.x - 1) {  // every other block has drawn its id: reset for the next call
@@ -131,7 +136,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const In* __restrict__ x, typ
 
   // ---- load and map kItems contiguous elements ----------------------------------
   const F f = MakeMap<F>::make(P);
-  const int64_t base = tile * kTile + (int64_t)threadIdx.x * kItems;
+  const int64_t base = tile * kTile + (int64_t)tid * kItems;
   const bool full = vec_ok && base + kItems <= n;
   C v[kItems];
   if (full) {
@@ -147,20 +152,18 @@ __global__ void __launch_bounds__(kThreads) k_scan(const In* __restrict__ x, typ
     for (int i = 0; i < kItems; ++i) v[i] = (base + i < n) ? f(S::cvt(x[base + i])) : C(0);
   }
 
-  // ---- serial scan of the thread's items, then warp and block scans -------------
-  T run[kItems];
+  // ---- thread total, warp scan of totals, block totals ------------------------------
   T acc = Op::zero();
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
-    if constexpr (std::is_same<Op, OpF32>::value) {  // TwoSum into (hi, lo); lo absorbs the errors
-      float s, e;
-      two_sum(acc.hi, v[i], s, e);
-      acc.hi = s;
+    if constexpr (std::is_same<Op, OpF32>::value) {  // TwoSum into (hi, lo)
+      float sm, e;
+      two_sum(acc.hi, v[i], sm, e);
+      acc.hi = sm;
       acc.lo += e;
     } else {
       acc = Op::add(acc, Op::lift(v[i]));
     }
-    run[i] = acc;
   }
   const T incl_lane = warp_incl_scan<Op>(acc, lane);
   T excl_lane = Op::shfl_up(incl_lane, 1);
@@ -174,80 +177,94 @@ __global__ void __launch_bounds__(kThreads) k_scan(const In* __restrict__ x, typ
     tile_tot = Op::add(tile_tot, s_warp[w]);
   }
 
-  // ---- decoupled look-back (warp 0) ---------------------------------------------
-  if (wid == 0) {
-    const Carry aggregate = Op::to_carry(tile_tot);
-    const bool stall = (tile == stall_tile);
-    Carry excl = Carry(0);
-    if (tile == 0) {
-      if (lane == 0 && !stall) {
-        incl[0] = aggregate;
-        st_release_u32(&ws.flags[0], tag | kFlagP);
-      }
-    } else {
-      if (lane == 0 && !stall) {
-        agg[tile] = aggregate;
-        st_release_u32(&ws.flags[tile], tag | kFlagA);
-      }
-      const uint64_t deadline = globaltimer_ns() + timeout_ns;
-      int64_t pos = tile - 1;
-      bool aborted = false;
-      while (true) {
-        const int64_t idx = pos - lane;
-        uint32_t st = 0;
-        while (true) {
-          if (idx >= 0) {
-            const uint32_t fl = ld_acquire_u32(&ws.flags[idx]);
-            st = ((fl & ~3u) == tag) ? (fl & 3u) : 0u;
-          } else {
-            st = kFlagP;  // before tile 0: an inclusive prefix of 0
-          }
-          if (__all_sync(kFull, st != 0u)) break;
-          int give_up = 0;
-          if (lane == 0) give_up = (globaltimer_ns() > deadline) || (ld_relaxed_u32(&hdr->abort) != 0u);
-          if (__shfl_sync(kFull, give_up, 0)) {
-            if (lane == 0 && !ld_relaxed_u32(&hdr->abort)) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)tile);
-            aborted = true;
+  // ---- decoupled look-back by the whole block: kThreads predecessors per round --------
+  const Carry aggregate = Op::to_carry(tile_tot);
+  const bool stall = (tile == stall_tile);
+  Carry excl = Carry(0);
+  if (tile == 0) {
+    if (tid == 0 && !stall) {
+      incl[0] = aggregate;
+      st_release_u32(&ws.flags[0], tag | kFlagP);
+    }
+  } else {
+    if (tid == 0 && !stall) {
+      agg[tile] = aggregate;
+      st_release_u32(&ws.flags[tile], tag | kFlagA);
+    }
+    const uint64_t deadline = globaltimer_ns() + timeout_ns;
+    int64_t pos = tile - 1;
+    while (true) {
+      const int64_t idx = pos - tid;
+      uint32_t st = kFlagP;  // before tile 0: an inclusive prefix of 0
+      int gave_up = 0;
+      if (idx >= 0) {
+        for (int polls = 0;; ++polls) {
+          const uint32_t fl = ld_acquire_u32(&ws.flags[idx]);
+          st = ((fl & ~3u) == tag) ? (fl & 3u) : 0u;
+          if (st) break;
+          if ((polls & 15) == 15 &&
+              (globaltimer_ns() > deadline || ld_relaxed_u32(&hdr->abort) != 0u)) {
+            gave_up = 1;
             break;
           }
-          __nanosleep(64);
+          if (polls > 4) __nanosleep(32);
         }
-        if (aborted) break;
-        Carry val = Carry(0);
-        if (idx >= 0) val = (st == kFlagP) ? incl[idx] : agg[idx];
-        const unsigned pmask = __ballot_sync(kFull, st == kFlagP);
-        const int j = __ffs(pmask) - 1;  // nearest predecessor holding an inclusive prefix
-        excl = Op::cadd(excl, warp_sum_carry<Op>((pmask == 0u || lane <= j) ? val : Carry(0)));
-        if (pmask) break;
-        pos -= 32;
       }
-      if (lane == 0 && !stall) {
-        incl[tile] = Op::cadd(excl, aggregate);
-        st_release_u32(&ws.flags[tile], tag | kFlagP);
+      if (__syncthreads_or(gave_up)) {
+        if (tid == 0 && !ld_relaxed_u32(&hdr->abort)) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)tile);
+        break;
       }
+      Carry val = Carry(0);
+      if (idx >= 0) val = (st == kFlagP) ? incl[idx] : agg[idx];
+      const unsigned pm = __ballot_sync(kFull, st == kFlagP);
+      if (lane == 0) s_first[wid] = pm ? __ffs(pm) - 1 : 32;
+      __syncthreads();
+      int first = kThreads;  // nearest predecessor holding an inclusive prefix (block-wide)
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w)
+        if (first == kThreads && s_first[w] < 32) first = w * 32 + s_first[w];
+      const Carry part = warp_sum_carry<Op>(tid <= first ? val : Carry(0));
+      if (lane == 0) s_red[wid] = part;
+      __syncthreads();
+      Carry round = Carry(0);
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) round = Op::cadd(round, s_red[w]);  // fixed order
+      excl = Op::cadd(excl, round);
+      __syncthreads();  // s_first / s_red are reused next round
+      if (first < kThreads) break;
+      pos -= kThreads;
     }
-    if (lane == 0) {
-      Carry c0 = Carry(0);
-      if (carry_in) c0 = Carry(*carry_in);
-      s_prefix = Op::cadd(c0, excl);
+    if (tid == 0 && !stall) {
+      incl[tile] = Op::cadd(excl, aggregate);
+      st_release_u32(&ws.flags[tile], tag | kFlagP);
     }
+  }
+  if (tid == 0) {
+    Carry c0 = Carry(0);
+    if (carry_in) c0 = Carry(*carry_in);
+    s_prefix = Op::cadd(c0, excl);
   }
   __syncthreads();
 
-  // ---- outputs ---------------------------------------------------------------------
+  // ---- outputs: the thread's running prefix on top of everything before it ----------
   Out o[kItems];
   if constexpr (std::is_same<Op, OpF32>::value) {
-    const FF basef = ff_add(ff_add(ff_from_double(s_prefix), warp_off), excl_lane);
+    FF run = ff_add(ff_add(ff_from_double(s_prefix), warp_off), excl_lane);
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {  // base + run_i, rounded once
-      float s, e;
-      two_sum(basef.hi, run[i].hi, s, e);
-      o[i] = s + (e + (basef.lo + run[i].lo));
+    for (int i = 0; i < kItems; ++i) {
+      float sm, e;
+      two_sum(run.hi, v[i], sm, e);
+      run.hi = sm;
+      run.lo += e;
+      o[i] = run.hi + run.lo;  // the compensated prefix, rounded once
     }
   } else {
-    const T b = Op::add(Op::add((T)s_prefix, warp_off), excl_lane);
+    T run = Op::add(Op::add((T)s_prefix, warp_off), excl_lane);
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) o[i] = Op::add(b, run[i]);
+    for (int i = 0; i < kItems; ++i) {
+      run = Op::add(run, Op::lift(v[i]));
+      o[i] = run;
+    }
   }
   if (full) {
     uint4* yv = reinterpret_cast<uint4*>(y + base);

@@ -65,6 +65,40 @@ __device__ __forceinline__ void write_slot(SegSlot* sl, long long seg, const Acc
   sl->through = through;
 }
 
+// Every warp has written its two slots.  The last block to arrive (ticket
+// after a fence) joins the pieces of each cut segment in warp order, in FP64.
+__device__ __forceinline__ void join_cut_segments(const RedOut& out, WsHeader* hdr, SegSlot* slots) {
+  const int64_t nw = (int64_t)gridDim.x * kWarps;
+  __shared__ bool last_block;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_block = atomicAdd(&hdr->ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last_block) return;
+  __threadfence();
+  for (int64_t w = threadIdx.x; w < nw; w += kThreads) {
+    const long long sg = __ldcg(&slots[2 * w + 1].seg);
+    if (sg < 0) continue;
+    double sum = __ldcg(&slots[2 * w + 1].sum);
+    float mn = __ldcg(&slots[2 * w + 1].mn), mx = __ldcg(&slots[2 * w + 1].mx);
+    for (int64_t w2 = w + 1; w2 < nw; ++w2) {
+      const SegSlot* h = &slots[2 * w2];
+      if (__ldcg(&h->seg) != sg) {
+        set_status(hdr, TR_ERR_DEVICE_ASSERT, (uint32_t)sg);
+        break;
+      }
+      sum += __ldcg(&h->sum);
+      mn = fminf(mn, __ldcg(&h->mn));
+      mx = fmaxf(mx, __ldcg(&h->mx));
+      if (!__ldcg(&h->through)) break;
+    }
+    store_result(out, sg, PartialF{sum, (double)mn, (double)mx}, true);
+  }
+  if (threadIdx.x == 0) hdr->ticket = 0;
+}
+
 template <class In, class F>
 __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x, int64_t n,
                                                         const int64_t* __restrict__ off, int64_t nseg, int64_t range,
@@ -72,7 +106,6 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
                                                         RedOut out, WsHeader* hdr, SegSlot* slots) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int64_t nw = (int64_t)gridDim.x * kWarps;
   const int64_t a = gw * range;
   const int64_t b = imin<int64_t>(n, a + range);
   const bool active = a < n || (n == 0 && gw == 0);
@@ -121,35 +154,213 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
     if (!wrote_tail) slots[2 * gw + 1].seg = -1;
   }
 
-  // ---- the last block joins the pieces of cut segments -----------------------------
-  __shared__ bool last_block;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last_block = atomicAdd(&hdr->ticket, 1u) == gridDim.x - 1;
+  join_cut_segments(out, hdr, slots);
+}
+
+
+// ---------------------------------------------------------------------------
+// The same walk with the loads decoupled from the arithmetic (16-byte aligned
+// x): every warp streams its range through a private ring of kStages chunks in
+// shared memory, filled by TMA bulk copies (one lane issues them, an mbarrier
+// per stage tracks the bytes), so kStages - 1 chunks of 2 KiB per warp are in
+// flight while the warp maps and accumulates the current one.  Segment
+// boundaries are handled inside a chunk: the common case (the chunk lies in one
+// segment) accumulates whole vectors; a chunk holding boundaries makes one
+// predicated pass per boundary and emits each finished segment.
+// ---------------------------------------------------------------------------
+constexpr int kStages = 4;
+constexpr int kChunkVec = 128;                          // 16-byte vectors per chunk (4 per lane)
+constexpr int kRingBytes = kStages * kChunkVec * 16;    // per warp
+constexpr int kTmaSmem = kWarps * kRingBytes;           // per block (dynamic)
+constexpr long long kTmaWaitLimit = 1ll << 22;          // mbarrier polls before giving up
+
+template <class In, class F>
+__global__ void __launch_bounds__(kThreads) k_segreduce_tma(const In* __restrict__ x, int64_t n,
+                                                            const int64_t* __restrict__ off, int64_t nseg,
+                                                            int64_t range, int /*x_aligned: always*/,
+                                                            const __grid_constant__ MapParams P, RedOut out,
+                                                            WsHeader* hdr, SegSlot* slots) {
+  using S = Storage<In>;
+  constexpr int V = S::kVec;
+  constexpr int E = 4 * V;  // elements per lane per chunk
+  extern __shared__ __align__(128) uint4 ring_all[];
+  __shared__ __align__(8) uint64_t bars[kWarps][kStages];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
+  const int64_t a = gw * range;
+  const int64_t b = imin<int64_t>(n, a + range);
+  const bool last = a < n && b == n;
+  const uint4* ring = ring_all + (size_t)wid * kStages * kChunkVec;
+  const uint32_t ring_s = smem_addr(ring), bar0 = smem_addr(&bars[wid][0]);
+  bool wrote_head = false, wrote_tail = false;
+  if (lane == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(bar0 + 8 * st, 1);
+    mbar_init_fence();
   }
-  __syncthreads();
-  if (!last_block) return;
-  __threadfence();
-  for (int64_t w = threadIdx.x; w < nw; w += kThreads) {
-    const long long sg = __ldcg(&slots[2 * w + 1].seg);
-    if (sg < 0) continue;
-    double sum = __ldcg(&slots[2 * w + 1].sum);
-    float mn = __ldcg(&slots[2 * w + 1].mn), mx = __ldcg(&slots[2 * w + 1].mx);
-    for (int64_t w2 = w + 1; w2 < nw; ++w2) {
-      const SegSlot* h = &slots[2 * w2];
-      if (__ldcg(&h->seg) != sg) {
-        set_status(hdr, TR_ERR_DEVICE_ASSERT, (uint32_t)sg);
+  __syncwarp();
+
+  if (a < n) {
+    const uint4* xv = reinterpret_cast<const uint4*>(x);
+    const int64_t va = a / V, vend = b / V;  // whole vectors [va, vend); elements [vend*V, b) are the tail
+    const int64_t nchunks = (vend - va + kChunkVec - 1) / kChunkVec;
+    auto issue = [&](int64_t k) {  // lane 0: fetch chunk k into its stage
+      const int st = (int)(k % kStages);
+      const int64_t v0 = va + k * kChunkVec;
+      const uint32_t bytes = (uint32_t)imin<int64_t>(kChunkVec, vend - v0) * 16u;
+      mbar_expect_tx(bar0 + 8 * st, bytes);
+      bulk_load(ring_s + (uint32_t)st * kChunkVec * 16u, xv + v0, bytes, bar0 + 8 * st);
+    };
+    if (lane == 0)
+      for (int64_t k = 0; k < imin<int64_t>(kStages, nchunks); ++k) issue(k);
+
+    const F f = MakeMap<F>::make(P);
+    const int64_t i0 = warp_lower_bound(off, nseg, a, lane);
+    int64_t s = (i0 <= nseg && __ldg(off + i0) == a) ? i0 : i0 - 1;
+    if (s < 0) s = 0;
+    int64_t wbase = s;
+    int64_t win = (wbase + lane <= nseg) ? __ldg(off + wbase + lane) : n;
+    int64_t lo_s = 0, hi_s = 0;
+    bool ok = true;
+    auto bounds = [&]() {  // lo_s, hi_s of segment s (warp-uniform); false on invalid offsets
+      if (s + 1 - wbase >= 32) {
+        wbase = s;
+        win = (wbase + lane <= nseg) ? __ldg(off + wbase + lane) : n;
+      }
+      lo_s = __shfl_sync(kFull, win, (int)(s - wbase));
+      hi_s = __shfl_sync(kFull, win, (int)(s + 1 - wbase));
+      if (hi_s < lo_s || lo_s < 0 || hi_s > n) {
+        if (lane == 0) set_status(hdr, TR_ERR_DEVICE_ASSERT, (uint32_t)s);
+        return false;
+      }
+      return true;
+    };
+    ok = s < nseg && bounds();
+    bool head_open = ok && lo_s < a;
+    Acc<float> acc;
+    auto finish = [&]() {  // segment s ends inside this range
+      const Acc<float>::W w = acc.warp();
+      if (lane == 0) {
+        if (head_open) {
+          write_slot(&slots[2 * gw], s, w, 0);
+          wrote_head = true;
+        } else {
+          store_result(out, s, Acc<float>::to_partial(w), true);
+        }
+      }
+      head_open = false;
+      acc = Acc<float>();
+    };
+    auto advance = [&]() { return ++s < nseg && bounds(); };
+    // accumulate one chunk's elements: e[u*V + j] is element base[u] + j, valid for j < nv[u]
+    auto process = [&](const float* e, const int64_t* base, const int* nv, int64_t ca, int64_t cb) {
+      if (hi_s >= cb) {  // the whole chunk lies in segment s
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (nv[u] == V) {
+            acc.template add_vec<V>(e + u * V);
+          } else {
+#pragma unroll
+            for (int j = 0; j < V; ++j)
+              if (j < nv[u]) acc.add(e[u * V + j]);
+          }
+        }
+        return true;
+      }
+      int64_t lo = ca;
+      while (true) {
+        const int64_t end = imin(hi_s, cb);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+          for (int j = 0; j < V; ++j) {
+            const int64_t idx = base[u] + j;
+            if (j < nv[u] && idx >= lo && idx < end) acc.add(e[u * V + j]);
+          }
+        }
+        if (hi_s > cb) return true;
+        finish();
+        if (!advance()) return false;
+        lo = lo_s;
+        if (lo_s >= cb) return true;
+      }
+    };
+
+    int64_t k = 0;
+    bool consumed = false;  // whether chunk k (where the loop stopped) was taken from the ring
+    for (; k < nchunks && ok; ++k) {
+      const int st = (int)(k % kStages);
+      if (!mbar_wait_bounded(bar0 + 8 * st, (uint32_t)((k / kStages) & 1), kTmaWaitLimit)) {
+        if (lane == 0) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)gw);
+        ok = false;
+        consumed = false;
         break;
       }
-      sum += __ldcg(&h->sum);
-      mn = fminf(mn, __ldcg(&h->mn));
-      mx = fmaxf(mx, __ldcg(&h->mx));
-      if (!__ldcg(&h->through)) break;
+      const int64_t v0 = va + k * kChunkVec;
+      const int cnt = (int)imin<int64_t>(kChunkVec, vend - v0);
+      float e[E];
+      int64_t base[4];
+      int nv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = u * 32 + lane;
+        nv[u] = j < cnt ? V : 0;
+        base[u] = (v0 + j) * V;
+        const uint4 r = j < cnt ? ring[st * kChunkVec + j] : make_uint4(0, 0, 0, 0);
+        S::unpack(r, e + u * V);
+      }
+      __syncwarp();
+      if (lane == 0 && k + kStages < nchunks) {
+        fence_async_smem();
+        issue(k + kStages);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) map_vec<V>(f, e + u * V);
+      ok = process(e, base, nv, v0 * V, (v0 + cnt) * V);
+      if (!ok) {
+        consumed = true;
+        break;
+      }
     }
-    store_result(out, sg, PartialF{sum, (double)mn, (double)mx}, true);
+    if (ok && vend * V < b) {  // ragged tail (last range only): one element per lane
+      float e[E];
+      int64_t base[4] = {vend * V + lane, 0, 0, 0};
+      int nv[4] = {vend * V + lane < b ? 1 : 0, 0, 0, 0};
+#pragma unroll
+      for (int i = 0; i < E; ++i) e[i] = 0.0f;
+      if (nv[0]) e[0] = f(S::cvt(x[base[0]]));
+      ok = process(e, base, nv, vend * V, b);
+    }
+    if (ok) {
+      if (hi_s == b) {  // the current segment ends exactly at the range end
+        finish();
+        while (advance() && last && lo_s == n) finish();  // empty segments at the very end
+      } else {          // it continues into the next range
+        const Acc<float>::W w = acc.warp();
+        if (lane == 0) {
+          if (head_open) {
+            write_slot(&slots[2 * gw], s, w, 1);
+            wrote_head = true;
+          } else {
+            write_slot(&slots[2 * gw + 1], s, w, 0);
+            wrote_tail = true;
+          }
+        }
+      }
+    }
+    // after an early stop, wait (bounded) for the copies still in flight before the shared
+    // memory is released: chunks issued but not yet taken from the ring
+    if (!ok) {
+      const int64_t from = consumed ? k + 1 : k;
+      const int64_t to = imin<int64_t>(nchunks, consumed ? k + kStages + 1 : k + kStages);
+      for (int64_t j = from; j < to; ++j)
+        mbar_wait_bounded(bar0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), kTmaWaitLimit);
+    }
   }
-  if (threadIdx.x == 0) hdr->ticket = 0;
+  if (lane == 0) {
+    if (!wrote_head) slots[2 * gw].seg = -1;
+    if (!wrote_tail) slots[2 * gw + 1].seg = -1;
+  }
+  join_cut_segments(out, hdr, slots);
 }
 
 }  // namespace
@@ -168,16 +379,28 @@ tr_status launch_segreduce(const MapParams& P, const void* x, tr_dtype xt, int64
     using In = decltype(in_tag);
     using F = decltype(map_tag);
     constexpr int V = Storage<In>::kVec;
-    auto kern = k_segreduce<In, F>;
-    const int64_t resident = (int64_t)dev_info().sm_count * blocks_per_sm((const void*)kern, kThreads);
+    const bool tma = x_aligned && n > 0;
+    auto kern = tma ? k_segreduce_tma<In, F> : k_segreduce<In, F>;
+    const size_t smem = tma ? (size_t)kTmaSmem : 0;
+    if (tma) {
+      static bool attr_set = false;  // per instantiation
+      if (!attr_set) {
+        tr_status s = cuda_status(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)smem),
+                                  "cudaFuncSetAttribute(k_segreduce_tma)");
+        if (s) return s;
+        attr_set = true;
+      }
+    }
+    const int64_t resident = (int64_t)dev_info().sm_count * blocks_per_sm((const void*)kern, kThreads, smem);
     const int64_t grid_full = std::min<int64_t>(resident, kMaxGrid);
     const int64_t quantum = 32 * V;  // range starts stay 16-byte aligned
     int64_t range = ceil_div(std::max<int64_t>(n, 1), grid_full * kWarps);
     range = ceil_div(range, quantum) * quantum;
     const int64_t warps_needed = std::max<int64_t>(1, ceil_div(n, range));
     const int64_t grid = ceil_div(warps_needed, kWarps);
-    kern<<<(unsigned)grid, kThreads, 0, st>>>(static_cast<const In*>(x), n, off, n_seg, range, x_aligned, P, out,
-                                               ws_header(e), reinterpret_cast<SegSlot*>(ws_body(e)));
+    kern<<<(unsigned)grid, kThreads, smem, st>>>(static_cast<const In*>(x), n, off, n_seg, range, x_aligned, P, out,
+                                                  ws_header(e), reinterpret_cast<SegSlot*>(ws_body(e)));
     return launch_status("k_segreduce");
   });
 }

@@ -20,10 +20,11 @@ namespace tr {
 
 namespace {
 
-// Largest input accepted: 16,384 tiles of 4,096 elements.
+// Largest input accepted: 2^26 elements.
 constexpr int64_t kNoAllocMaxN = int64_t(1) << 26;
-// Header + per-tile flags and two 8-byte values per tile, 256-byte aligned
-// (the layout tr_scan's launcher expects for this many tiles).
+// Header + per-tile flags and two 8-byte values per tile for up to 16,384
+// tiles (tr_scan's tiles hold at least 4,096 elements, so 2^26 elements never
+// need more), 256-byte aligned as tr_scan's launcher lays them out.
 constexpr size_t kNoAllocScratchBytes = 256 + (size_t)(16384) * 4 + 2 * (size_t)(16384) * 8;
 
 // The scratch.  In host code this name is only a stand-in for the symbol, not

@@ -237,8 +237,8 @@ def scan_dev(B, m, x, yt_torch, carry=None, out=None):
 
 
 @pytest.mark.parametrize("kind", ["splitmix32", "xorshift32", "identity"])
-@pytest.mark.parametrize("n,off", [(1, 0), (31, 0), (4095, 0), (4096, 0), (4097, 0), (12289, 0), (1 << 20, 0),
-                                   (1_000_003, 0), (100_001, 1), (8193, 2)])
+@pytest.mark.parametrize("n,off", [(1, 0), (31, 0), (4095, 0), (4097, 0), (8191, 0), (8192, 0), (8193, 0),
+                                   (24577, 0), (1 << 20, 0), (1_000_003, 0), (100_001, 1), (8193, 2)])
 def test_scan_u32_bitexact(orc, B, kind, n, off):
     x = I.u32(I.rng("mixer_u32_scan", n), n)
     xd = to_dev(x, offset=off)
@@ -309,7 +309,7 @@ def test_scan_timeout_reports_and_recovers(orc, B):
     """A tile that never publishes makes its successor's bounded wait run out:
     tr_check reports TR_ERR_TIMEOUT, the context stays usable, and a
     re-initialised workspace scans correctly.  No trap, no hang."""
-    n = 64 * 4096
+    n = 64 * 8192
     x = I.u32(I.rng("misc", 11), n)
     xd = to_dev(x)
     ws = B.workspace(B.tr_scan_workspace_size(n, B.TR_U32, B.TR_U32))
@@ -429,3 +429,23 @@ def test_segreduce_bad_offsets_reported(B):
     with pytest.raises(B.TrError) as e:
         B.tr_check(ex)
     assert e.value.status == 7
+
+
+@pytest.mark.parametrize("dt", ["f32", "f16"])
+def test_segreduce_boundaries_on_chunk_and_range_edges(orc, B, dt):
+    """Segment ends placed exactly on (and one off) the 2 KiB streaming-chunk
+    edges and on multiples of the per-warp range quantum, plus runs of empty
+    segments sitting on those edges."""
+    m = MAPS[4]
+    n = (1 << 22) + 77
+    th, xh = host_input(dt, n, seed=123)
+    V = 4 if dt == "f32" else 8
+    edges = set()
+    for q in (128 * V, 32 * V * 14, 32 * V * 56):
+        for k in range(1, n // q, 7):
+            for d in (-1, 0, 1):
+                edges.add(k * q + d)
+    edges = sorted(e for e in edges if 0 < e < n)
+    off = np.concatenate([[0], edges, edges[::50], [n, n]]).astype(np.int64)
+    off.sort()
+    check_seg(orc, m, xh, off, segreduce_dev(B, m, th.cuda(), off))
