@@ -70,6 +70,7 @@ __device__ __forceinline__ void write_slot(SegSlot* sl, long long seg, const Acc
 __device__ __forceinline__ void join_cut_segments(const RedOut& out, WsHeader* hdr, SegSlot* slots) {
   const int64_t nw = (int64_t)gridDim.x * kWarps;
   __shared__ bool last_block;
+  __threadfence();  // each slot writer's records are visible device-wide before the ticket
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
@@ -308,13 +309,14 @@ __global__ void __launch_bounds__(kThreads) k_segreduce_tma(const In* __restrict
         const uint4 r = j < cnt ? ring[st * kChunkVec + j] : make_uint4(0, 0, 0, 0);
         S::unpack(r, e + u * V);
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) map_vec<V>(f, e + u * V);
+      // the stage's values are consumed (used above): hand the stage back to the copy engine
       __syncwarp();
       if (lane == 0 && k + kStages < nchunks) {
         fence_async_smem();
         issue(k + kStages);
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) map_vec<V>(f, e + u * V);
       ok = process(e, base, nv, v0 * V, (v0 + cnt) * V);
       if (!ok) {
         consumed = true;
@@ -331,21 +333,30 @@ __global__ void __launch_bounds__(kThreads) k_segreduce_tma(const In* __restrict
       ok = process(e, base, nv, vend * V, b);
     }
     if (ok) {
-      if (hi_s == b) {  // the current segment ends exactly at the range end
-        finish();
-        while (advance() && last && lo_s == n) finish();  // empty segments at the very end
-      } else {          // it continues into the next range
-        const Acc<float>::W w = acc.warp();
-        if (lane == 0) {
-          if (head_open) {
-            write_slot(&slots[2 * gw], s, w, 1);
-            wrote_head = true;
-          } else {
-            write_slot(&slots[2 * gw + 1], s, w, 0);
-            wrote_tail = true;
+      if (lo_s < b) {     // segment s started in (or before) this range
+        if (hi_s == b) {  // ... and ends exactly at its end
+          finish();
+          advance();
+        } else {          // ... and continues into the next range
+          const Acc<float>::W w = acc.warp();
+          if (lane == 0) {
+            if (head_open) {
+              write_slot(&slots[2 * gw], s, w, 1);
+              wrote_head = true;
+            } else {
+              write_slot(&slots[2 * gw + 1], s, w, 0);
+              wrote_tail = true;
+            }
           }
         }
       }
+      // a segment starting at b belongs to the next range; only the last range also
+      // emits the empty segments sitting at n
+      if (last)
+        while (s < nseg && lo_s == n && hi_s == n) {
+          finish();
+          if (!advance()) break;
+        }
     }
     // after an early stop, wait (bounded) for the copies still in flight before the shared
     // memory is released: chunks issued but not yet taken from the ring
