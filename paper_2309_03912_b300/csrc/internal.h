@@ -1,6 +1,7 @@
 // internal.h -- host-side helpers shared by the launchers of libtr.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,6 +47,13 @@ inline char* ws_body(const tr_exec* e) { return static_cast<char*>(e->workspace)
 inline cudaStream_t stream_of(const tr_exec* e) { return static_cast<cudaStream_t>(e->stream); }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// 2-D tiled tensor map over a row-major array: `rows` rows of `inner`
+// elements, `row_bytes` apart; boxes of box_inner x box_rows elements.
+// (cuTensorMapEncodeTiled through the runtime's driver entry point.)
+tr_status make_tensor_map_2d(CUtensorMap* out, const void* base, CUtensorMapDataType type, uint64_t inner,
+                             uint64_t rows, uint64_t row_bytes, uint32_t box_inner, uint32_t box_rows,
+                             CUtensorMapSwizzle swizzle);
 
 // ---- launchers (one per kernel family) ------------------------------------
 size_t reduce_ws_bytes(int64_t n, tr_dtype xt);

@@ -176,7 +176,7 @@ constexpr int kTmaSmem = kWarps * kRingBytes;           // per block (dynamic)
 constexpr long long kTmaWaitLimit = 1ll << 22;          // mbarrier polls before giving up
 
 template <class In, class F>
-__global__ void __launch_bounds__(kThreads) k_segreduce_tma(const In* __restrict__ x, int64_t n,
+__global__ void __launch_bounds__(kThreads, 3) k_segreduce_tma(const In* __restrict__ x, int64_t n,
                                                             const int64_t* __restrict__ off, int64_t nseg,
                                                             int64_t range, int /*x_aligned: always*/,
                                                             const __grid_constant__ MapParams P, RedOut out,
@@ -252,36 +252,44 @@ __global__ void __launch_bounds__(kThreads) k_segreduce_tma(const In* __restrict
       acc = Acc<float>();
     };
     auto advance = [&]() { return ++s < nseg && bounds(); };
-    // accumulate one chunk's elements: e[u*V + j] is element base[u] + j, valid for j < nv[u]
-    auto process = [&](const float* e, const int64_t* base, const int* nv, int64_t ca, int64_t cb) {
-      if (hi_s >= cb) {  // the whole chunk lies in segment s
+    // one chunk: vectors [v0, v0 + cnt) of x, staged in ring stage st
+    auto chunk = [&](int st, int64_t v0, int cnt) -> bool {
+      const int64_t ca = v0 * V, cb = (v0 + cnt) * V;
+      const uint4* src = ring + st * kChunkVec;
+      if (hi_s >= cb) {  // common case: the whole chunk lies in segment s
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          if (nv[u] == V) {
-            acc.template add_vec<V>(e + u * V);
-          } else {
-#pragma unroll
-            for (int j = 0; j < V; ++j)
-              if (j < nv[u]) acc.add(e[u * V + j]);
+          const int j = u * 32 + lane;
+          if (j < cnt) {
+            float e[V];
+            S::unpack(src[j], e);
+            map_vec<V>(f, e);
+            acc.template add_vec<V>(e);
           }
         }
         return true;
       }
-      int64_t lo = ca;
+      // boundaries inside the chunk: one predicated pass per segment piece, re-reading
+      // the stage; indices are chunk-relative
+      int lo = 0;
       while (true) {
-        const int64_t end = imin(hi_s, cb);
+        const int end = (int)(imin(hi_s, cb) - ca);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
+          const int j = u * 32 + lane, e0 = j * V;
+          if (j < cnt && e0 + V > lo && e0 < end) {
+            float e[V];
+            S::unpack(src[j], e);
+            map_vec<V>(f, e);
 #pragma unroll
-          for (int j = 0; j < V; ++j) {
-            const int64_t idx = base[u] + j;
-            if (j < nv[u] && idx >= lo && idx < end) acc.add(e[u * V + j]);
+            for (int q = 0; q < V; ++q)
+              if (e0 + q >= lo && e0 + q < end) acc.add(e[q]);
           }
         }
         if (hi_s > cb) return true;
         finish();
         if (!advance()) return false;
-        lo = lo_s;
+        lo = (int)(lo_s - ca);
         if (lo_s >= cb) return true;
       }
     };
@@ -297,40 +305,41 @@ __global__ void __launch_bounds__(kThreads) k_segreduce_tma(const In* __restrict
         break;
       }
       const int64_t v0 = va + k * kChunkVec;
-      const int cnt = (int)imin<int64_t>(kChunkVec, vend - v0);
-      float e[E];
-      int64_t base[4];
-      int nv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = u * 32 + lane;
-        nv[u] = j < cnt ? V : 0;
-        base[u] = (v0 + j) * V;
-        const uint4 r = j < cnt ? ring[st * kChunkVec + j] : make_uint4(0, 0, 0, 0);
-        S::unpack(r, e + u * V);
+      ok = chunk(st, v0, (int)imin<int64_t>(kChunkVec, vend - v0));
+      if (!ok) {
+        consumed = true;
+        break;
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) map_vec<V>(f, e + u * V);
-      // the stage's values are consumed (used above): hand the stage back to the copy engine
+      // the stage has been read by every lane: hand it back to the copy engine
       __syncwarp();
       if (lane == 0 && k + kStages < nchunks) {
         fence_async_smem();
         issue(k + kStages);
       }
-      ok = process(e, base, nv, v0 * V, (v0 + cnt) * V);
-      if (!ok) {
-        consumed = true;
-        break;
-      }
     }
     if (ok && vend * V < b) {  // ragged tail (last range only): one element per lane
-      float e[E];
-      int64_t base[4] = {vend * V + lane, 0, 0, 0};
-      int nv[4] = {vend * V + lane < b ? 1 : 0, 0, 0, 0};
-#pragma unroll
-      for (int i = 0; i < E; ++i) e[i] = 0.0f;
-      if (nv[0]) e[0] = f(S::cvt(x[base[0]]));
-      ok = process(e, base, nv, vend * V, b);
+      const int64_t ca = vend * V;
+      const int tl = (int)(b - ca);
+      const bool has = lane < tl;
+      const float ev = has ? f(S::cvt(x[ca + lane])) : 0.0f;
+      if (hi_s >= b) {
+        if (has) acc.add(ev);
+      } else {
+        int lo = 0;
+        while (true) {
+          const int end = (int)(imin(hi_s, b) - ca);
+          if (has && lane >= lo && lane < end) acc.add(ev);
+          if (hi_s > b) break;
+          finish();
+          if (!advance()) {
+            ok = false;
+            break;
+          }
+          lo = (int)(lo_s - ca);
+          if (lo_s >= b) break;
+        }
+        if (!ok) k = nchunks, consumed = false;  // nothing is in flight any more
+      }
     }
     if (ok) {
       if (lo_s < b) {     // segment s started in (or before) this range
@@ -362,7 +371,7 @@ __global__ void __launch_bounds__(kThreads) k_segreduce_tma(const In* __restrict
     // memory is released: chunks issued but not yet taken from the ring
     if (!ok) {
       const int64_t from = consumed ? k + 1 : k;
-      const int64_t to = imin<int64_t>(nchunks, consumed ? k + kStages + 1 : k + kStages);
+      const int64_t to = imin<int64_t>(nchunks, k + kStages);
       for (int64_t j = from; j < to; ++j)
         mbar_wait_bounded(bar0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), kTmaWaitLimit);
     }

@@ -86,8 +86,8 @@ extern "C" tr_status tr_scan_noalloc(const tr_map_desc* map, const void* x, tr_d
   if ((s = scratch_address(&scratch))) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // The array keeps the previous call's contents.  Clear the error words
-  // (status, detail, abort) and the two counters; the tile flags need no
-  // clearing because they carry the call epoch kept in the header.
+  // (status, detail, abort) and the two counters; the scan itself clears its
+  // tile flags before it starts.
   auto* hdr = static_cast<WsHeader*>(scratch);
   if ((s = cuda_status(cudaMemsetAsync(hdr, 0, 3 * sizeof(uint32_t), st), "cudaMemsetAsync(status)"))) return s;
   if ((s = cuda_status(cudaMemsetAsync(&hdr->ticket, 0, 2 * sizeof(uint32_t), st), "cudaMemsetAsync(counters)")))
