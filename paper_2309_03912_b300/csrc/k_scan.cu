@@ -16,9 +16,9 @@
 //   * every wait is bounded by a %globaltimer deadline and an abort word: on
 //     expiry the block records TR_ERR_TIMEOUT and finishes instead of hanging.
 // Each call clears the tile flags and the tile counter with two memsets on
-// the stream (graph-capturable) before the kernel.  Aligned inputs of at least
-// one tile take a persistent form whose blocks keep the next tile's TMA load
-// in flight while they scan and look back on the current one.
+// the stream (graph-capturable) before the kernel.  Predecessor flags are
+// polled with relaxed loads; one acquire fence per thread and round orders the
+// reads of the values behind them.
 //
 // Arithmetic: u32 wraps modulo 2^32; u32 -> u64 is exact; float scans keep
 // float-float (hi, lo) pairs inside a tile, FP64 between tiles, and round each
@@ -135,16 +135,17 @@ __device__ __forceinline__ typename Op::Carry block_lookback(int64_t tile, typen
     const int64_t idx = pos - tid;
     uint32_t st = kFlagP;  // before tile 0: an inclusive prefix of 0
     int gave_up = 0;
-    if (idx >= 0) {
+    if (idx >= 0) {  // relaxed polling; one acquire fence once the flag is seen
       for (int polls = 0;; ++polls) {
-        st = ld_acquire_u32(&ws.flags[idx]) & 3u;
+        st = ld_relaxed_u32(&ws.flags[idx]) & 3u;
         if (st) break;
         if ((polls & 15) == 15 && (globaltimer_ns() > deadline || ld_relaxed_u32(&hdr->abort) != 0u)) {
           gave_up = 1;
           break;
         }
-        if (polls > 4) __nanosleep(32);
+        if (polls > 8) __nanosleep(20);
       }
+      fence_acq_rel_gpu();
     }
     if (__syncthreads_or(gave_up)) {
       if (tid == 0 && !ld_relaxed_u32(&hdr->abort)) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)tile);
@@ -295,108 +296,6 @@ __global__ void __launch_bounds__(kThreads) k_scan(const In* __restrict__ x, typ
   store_items(y, base, n, vec_ok, o);
 }
 
-// Persistent form (16-byte aligned x, n >= one tile): each block claims tiles
-// from the counter and keeps the next tile's load in flight -- a 2-D tensor
-// TMA copy (rows of kItems elements, 128-byte or 64-byte swizzle) into the
-// other of two shared-memory buffers -- while it scans and looks back on the
-// current tile.  Thread t reads row t of the tile; the swizzle spreads a
-// quarter-warp's 16-byte reads over distinct banks.
-template <class In, class F, class Op>
-__global__ void __launch_bounds__(kThreads) k_scan_tma(const __grid_constant__ CUtensorMap tmap,
-                                                       const In* __restrict__ x, typename Op::Out* y, int64_t n,
-                                                       int y_vec, const __grid_constant__ MapParams P, WsHeader* hdr,
-                                                       ScanWs ws, const typename Op::Out* carry_in,
-                                                       uint64_t timeout_ns, int64_t stall_tile, uint32_t ntiles) {
-  using S = Storage<In>;
-  using C = typename S::C;
-  using T = typename Op::T;
-  using Carry = typename Op::Carry;
-  using Out = typename Op::Out;
-  constexpr int V = S::kVec;
-  constexpr int kRowBytes = kItems * (int)sizeof(In);  // 128 (4-byte types) or 64 (2-byte types)
-  constexpr int kChunks = kRowBytes / 16;
-  constexpr uint32_t kBufBytes = kThreads * kRowBytes;
-  static_assert(kRowBytes == 128 || kRowBytes == 64, "row size");
-
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* buf = smem_raw + ((1024 - (smem_addr(smem_raw) & 1023)) & 1023);
-  __shared__ __align__(8) uint64_t bars[2];
-  __shared__ uint32_t s_tiles[2];
-  __shared__ int s_bad;
-  __shared__ T s_warp[kWarps];
-  __shared__ LookbackSmem<Op> s_lb;
-  const int tid = threadIdx.x;
-  const uint32_t buf_s = smem_addr(buf), bar_s = smem_addr(&bars[0]);
-  const int64_t nrows = n / kItems;  // rows covered by the tensor map
-  auto issue = [&](uint32_t t, int b) {  // thread 0: load tile t into buffer b
-    mbar_expect_tx(bar_s + 8 * b, kBufBytes);
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(buf_s + (uint32_t)b * kBufBytes),
-        "l"(&tmap), "r"(0), "r"((int)(t * kThreads)), "r"(bar_s + 8 * b)
-        : "memory");
-  };
-  if (tid == 0) {
-    mbar_init(bar_s, 1);
-    mbar_init(bar_s + 8, 1);
-    mbar_init_fence();
-    const uint32_t t0 = atomicAdd(&hdr->tile_counter, 1u);
-    const uint32_t t1 = t0 < ntiles ? atomicAdd(&hdr->tile_counter, 1u) : ntiles;
-    s_tiles[0] = t0;
-    s_tiles[1] = t1;
-    s_bad = 0;
-    if (t0 < ntiles) issue(t0, 0);
-    if (t1 < ntiles) issue(t1, 1);
-  }
-  __syncthreads();
-  const F f = MakeMap<F>::make(P);
-  const Carry c0 = carry_in ? Carry(*carry_in) : Carry(0);
-  for (uint32_t i = 0;; ++i) {
-    const int b = (int)(i & 1u);
-    const uint32_t tile = s_tiles[b];
-    if (tile >= ntiles) break;
-    const bool landed = mbar_wait_bounded(bar_s + 8 * b, (i >> 1) & 1u, 1ll << 22);
-    if (__syncthreads_or(landed ? 0 : 1)) {  // a copy never completed: record, drain, stop
-      if (tid == 0) {
-        set_status(hdr, TR_ERR_TIMEOUT, tile);
-        if (s_tiles[b ^ 1] < ntiles) mbar_wait_bounded(bar_s + 8 * (b ^ 1), ((i + 1) >> 1) & 1u, 1ll << 22);
-      }
-      break;
-    }
-    // row tid of the tile: kItems elements, the swizzled 16-byte chunks read back in order
-    const int64_t row = (int64_t)tile * kThreads + tid;
-    const int64_t base = row * kItems;
-    C v[kItems];
-    const unsigned char* rp = buf + (uint32_t)b * kBufBytes + (uint32_t)tid * kRowBytes;
-    const int sw = kRowBytes == 128 ? (tid & 7) : ((tid >> 1) & 3);
-#pragma unroll
-    for (int c = 0; c < kChunks; ++c) S::unpack(*reinterpret_cast<const uint4*>(rp + ((c ^ sw) * 16)), v + c * V);
-    if (row >= nrows) {  // beyond the tensor map: the ragged tail (row == nrows) comes from global memory
-#pragma unroll
-      for (int q = 0; q < kItems; ++q) v[q] = (base + q < n) ? S::cvt(x[base + q]) : C(0);
-    }
-    map_vec<kItems>(f, v);
-    __syncthreads();  // buffer b and s_tiles[b] have been read by every thread
-    if (tid == 0) {
-      uint32_t nxt = ntiles;  // claim the tile after the next one (claims stop once past the end)
-      if (s_tiles[b ^ 1] < ntiles) nxt = atomicAdd(&hdr->tile_counter, 1u);
-      s_tiles[b] = nxt;
-      if (nxt < ntiles) {
-        fence_async_smem();
-        issue(nxt, b);
-      }
-    }
-    T warp_off, excl_lane, tile_tot;
-    scan_totals<Op>(v, s_warp, warp_off, excl_lane, tile_tot);
-    const Carry excl =
-        block_lookback<Op>(tile, Op::to_carry(tile_tot), ws, hdr, timeout_ns, tile == stall_tile, s_lb);
-    Out o[kItems];
-    scan_outputs<Op>(v, Op::cadd(c0, excl), warp_off, excl_lane, o);
-    store_items(y, base, n, y_vec != 0, o);
-    __syncthreads();  // s_warp is reused by the next tile
-  }
-}
-
 }  // namespace
 
 size_t scan_ws_bytes(int64_t n, tr_dtype, tr_dtype) {
@@ -415,7 +314,6 @@ tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, t
   const ScanWs ws{reinterpret_cast<uint32_t*>(ws_body(e)), ws_body(e) + flags_b, ws_body(e) + flags_b + vals_b};
   const uint64_t timeout_ns = (uint64_t)(e->wait_timeout_us ? e->wait_timeout_us : 1000000u) * 1000ull;
   const int vec_ok = aligned_to(x, 16) && aligned_to(y, 16);
-  const bool tma = aligned_to(x, 16) && n >= kTile;
   cudaStream_t st = stream_of(e);
   WsHeader* hdr = ws_header(e);
   const int64_t stall = e->debug_stall_tile;
@@ -429,37 +327,10 @@ tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, t
       using In = decltype(in_tag);
       using F = decltype(map_tag);
       using Out = typename Op::Out;
-      if (!tma) {
-        k_scan<In, F, Op><<<(unsigned)tiles, kThreads, 0, st>>>(static_cast<const In*>(x), static_cast<Out*>(y), n,
-                                                                vec_ok, P, hdr, ws, static_cast<const Out*>(carry),
-                                                                timeout_ns, stall);
-        return launch_status("k_scan");
-      }
-      constexpr int kRowBytes = kItems * (int)sizeof(In);
-      const size_t smem = 2 * (size_t)kThreads * kRowBytes + 1024;
-      auto kern = k_scan_tma<In, F, Op>;
-      static bool attr_set = false;
-      if (!attr_set) {
-        tr_status r = cuda_status(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)smem),
-                                  "cudaFuncSetAttribute(k_scan_tma)");
-        if (r) return r;
-        attr_set = true;
-      }
-      CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-      if (std::is_same<In, __half>::value) dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-      if (std::is_same<In, __nv_bfloat16>::value) dt = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-      if (std::is_same<In, uint32_t>::value) dt = CU_TENSOR_MAP_DATA_TYPE_UINT32;
-      CUtensorMap tm;
-      tr_status r = make_tensor_map_2d(&tm, x, dt, kItems, (uint64_t)(n / kItems), (uint64_t)kRowBytes, kItems,
-                                       kThreads, kRowBytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
-      if (r) return r;
-      const int64_t resident = (int64_t)dev_info().sm_count * blocks_per_sm((const void*)kern, kThreads, smem);
-      const int64_t grid = std::min<int64_t>(tiles, resident);
-      kern<<<(unsigned)grid, kThreads, smem, st>>>(tm, static_cast<const In*>(x), static_cast<Out*>(y), n,
-                                                   aligned_to(y, 16) ? 1 : 0, P, hdr, ws,
-                                                   static_cast<const Out*>(carry), timeout_ns, stall, (uint32_t)tiles);
-      return launch_status("k_scan_tma");
+      k_scan<In, F, Op><<<(unsigned)tiles, kThreads, 0, st>>>(static_cast<const In*>(x), static_cast<Out*>(y), n,
+                                                              vec_ok, P, hdr, ws, static_cast<const Out*>(carry),
+                                                              timeout_ns, stall);
+      return launch_status("k_scan");
     };
   };
   if (xt == TR_U32 && yt == TR_U32) return dispatch_u32_map(P, go(OpU32{}));

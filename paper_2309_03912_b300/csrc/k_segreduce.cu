@@ -256,7 +256,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_segreduce_tma(const In* __restr
     auto chunk = [&](int st, int64_t v0, int cnt) -> bool {
       const int64_t ca = v0 * V, cb = (v0 + cnt) * V;
       const uint4* src = ring + st * kChunkVec;
-      if (hi_s >= cb) {  // common case: the whole chunk lies in segment s
+      if (hi_s >= cb && cnt == kChunkVec) {  // common case: a full chunk inside segment s
+        float e[4 * V];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) S::unpack(src[u * 32 + lane], e + u * V);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) map_vec<V>(f, e + u * V);  // independent chains interleave
+        acc.template add_vec<4 * V>(e);
+        return true;
+      }
+      if (hi_s >= cb) {  // a partial chunk inside segment s
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int j = u * 32 + lane;

@@ -19,8 +19,9 @@
 //     accumulator and commits them to an mbarrier; the other CTA on the SM
 //     overlaps its own tile with this one.
 //   * The epilogue reads the accumulator with tcgen05.ld (32 lanes x 32
-//     columns per warp and step) and writes each row's 32 columns as one
-//     128-byte line with streaming stores.
+//     columns per warp and step), stages each 32 x 32 block in shared memory
+//     in the 128-byte-swizzled layout and writes it with one 2-D TMA tensor
+//     store (bulk async-groups, two staging blocks per warp in rotation).
 //   Every mbarrier wait is bounded; on expiry the CTA records TR_ERR_TIMEOUT in
 //   the workspace, stops, and still frees its TMEM.
 //
@@ -73,7 +74,8 @@ constexpr uint32_t kLBO = 128;   // between K-adjacent core matrices
 constexpr uint32_t kSBO = 512;   // between 8-row groups (K = 32: 4 core matrices)
 constexpr uint32_t kABytes = kTileM * kK * 2;  // 8 KiB per bf16 part
 constexpr uint32_t kBBytes = kTileN * kK * 2;  // 16 KiB per bf16 part
-constexpr uint32_t kSmemUsed = 2 * kABytes + 2 * kBBytes + 64;
+constexpr uint32_t kStageBytes = 32 * 32 * 4;                  // one warp's 32 x 32 FP32 output block
+constexpr uint32_t kSmemUsed = 2 * kABytes + 2 * kBBytes + 4 * 2 * kStageBytes + 64;
 // request more dynamic shared memory than used so that at most two CTAs share
 // an SM: two 256-column accumulators fill the SM's 512 TMEM columns
 constexpr uint32_t kSmemRequest = 96 * 1024;
@@ -163,16 +165,18 @@ __device__ __forceinline__ void store_split_row(unsigned char* hi, unsigned char
   }
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const float* __restrict__ x, int64_t m,
+__global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_constant__ CUtensorMap ymap,
+                                                             const float* __restrict__ x, int64_t m,
                                                              const float* __restrict__ coef, int deg, int64_t npoly,
-                                                             float* __restrict__ y, WsHeader* hdr) {
+                                                             WsHeader* hdr) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   unsigned char* sAh = base;
   unsigned char* sAl = sAh + kABytes;
   unsigned char* sBh = sAl + kABytes;
   unsigned char* sBl = sBh + kBBytes;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sBl + kBBytes);
+  unsigned char* sOut = sBl + kBBytes;  // 4 warps x 2 staging blocks, 1024-byte aligned
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sOut + 4 * 2 * kStageBytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -246,20 +250,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const float* __rest
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
-    const int64_t row = m0 + warp * 32 + lane;
-    float* yrow = y + row * npoly + n0;
+    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31.  Each 32 x 32 block goes
+    // registers -> swizzled shared staging (row r's 16-byte chunk q at q ^ (r % 8), the
+    // 128-byte swizzle of the tensor map) -> one TMA tensor store issued by lane 0.
+    // Two staging blocks per warp alternate; lane 0 waits until the store issued two
+    // blocks earlier has finished reading its block before it is overwritten.
 #pragma unroll 1
     for (int c = 0; c < kTileN / 32; ++c) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-      uint4* dst = reinterpret_cast<uint4*>(yrow + c * 32);
+      unsigned char* stg = sOut + (uint32_t)(warp * 2 + (c & 1)) * kStageBytes;
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+      __syncwarp();
 #pragma unroll
-      for (int q = 0; q < 8; ++q) st_stream(dst + q, pack16(v + 4 * q));
+      for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<uint4*>(stg + lane * 128 + ((q ^ (lane & 7)) * 16)) = pack16(v + 4 * q);
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile(
+            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(&ymap),
+            "r"((int)(n0 + c * 32)), "r"((int)(m0 + warp * 32)), "r"(smem_u32(stg))
+            : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();  // TMEM and the A / B tiles are free for the next tile
   }
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // this warp's stores are done
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
@@ -307,9 +326,14 @@ tr_status tr_vandermonde(const float* x, int64_t m, const float* coef, int32_t d
       cudaFuncSetAttribute(k_vander_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemRequest),
       "cudaFuncSetAttribute(k_vander_tc)");
   if (s) return s;
+  if (m > 0x7FFFFFFF || npoly > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "m or npoly beyond 32-bit coordinates");
+  CUtensorMap ymap;
+  if ((s = make_tensor_map_2d(&ymap, y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (uint64_t)npoly, (uint64_t)m,
+                              (uint64_t)npoly * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B)))
+    return s;
   const int64_t tiles = (m / kTileM) * (npoly / kTileN);
   const int64_t grid = std::min<int64_t>(tiles, 2 * (int64_t)dev_info().sm_count);
-  k_vander_tc<<<(unsigned)grid, kTcThreads, kSmemRequest, st>>>(x, m, coef, deg, npoly, y, ws_header(e));
+  k_vander_tc<<<(unsigned)grid, kTcThreads, kSmemRequest, st>>>(ymap, x, m, coef, deg, npoly, ws_header(e));
   return launch_status("k_vander_tc");
 }
 
