@@ -25,12 +25,26 @@ struct PartialU {
 template <class C>
 struct Acc;
 
+// Pairwise sum of V values.  From four values up the first levels run on
+// packed pairs (add.rn.f32x2: pair j of the first half plus pair j of the
+// second half), so every value still passes through log2(V) additions.
 template <int V>
 __device__ __forceinline__ float pairwise(const float* v) {
   if constexpr (V == 1) {
     return v[0];
+  } else if constexpr (V == 2 || V % 4 != 0) {
+    return pairwise<V / 2>(v) + pairwise<V - V / 2>(v + V / 2);
   } else {
-    return pairwise<V / 2>(v) + pairwise<V / 2>(v + V / 2);
+    unsigned long long p[V / 2];
+#pragma unroll
+    for (int j = 0; j < V / 2; ++j) p[j] = pack_f32x2(v[2 * j], v[2 * j + 1]);
+#pragma unroll
+    for (int w = V / 4; w >= 1; w /= 2)
+#pragma unroll
+      for (int j = 0; j < w; ++j) p[j] = add_f32x2(p[j], p[j + w]);
+    float lo, hi;
+    unpack_f32x2(p[0], lo, hi);
+    return lo + hi;
   }
 }
 
@@ -48,9 +62,34 @@ struct Acc<float> {
   __device__ __forceinline__ void add_vec(const float* v) {
     k.add(pairwise<V>(v));
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-      mn = fminf(mn, v[i]);
-      mx = fmaxf(mx, v[i]);
+    for (int i = 0; i + 1 < V; i += 2) {
+      mn = min3f(mn, v[i], v[i + 1]);
+      mx = max3f(mx, v[i], v[i + 1]);
+    }
+    if constexpr (V % 2 == 1) {
+      mn = fminf(mn, v[V - 1]);
+      mx = fmaxf(mx, v[V - 1]);
+    }
+  }
+  // Only the values v[i] with take(i) true (take: index -> bool, evaluated
+  // for compile-time i); the others are never combined.
+  template <int V, class Take>
+  __device__ __forceinline__ void add_if(const float* v, Take take) {
+    float t[V];
+#pragma unroll
+    for (int i = 0; i < V; ++i) t[i] = take(i) ? v[i] : 0.0f;
+    k.add(pairwise<V>(t));
+#pragma unroll
+    for (int i = 0; i + 1 < V; i += 2) {
+      const bool a = take(i), b = take(i + 1);
+      mn = min3f(mn, a ? v[i] : INFINITY, b ? v[i + 1] : INFINITY);
+      mx = max3f(mx, a ? v[i] : -INFINITY, b ? v[i + 1] : -INFINITY);
+    }
+    if constexpr (V % 2 == 1) {
+      if (take(V - 1)) {
+        mn = fminf(mn, v[V - 1]);
+        mx = fmaxf(mx, v[V - 1]);
+      }
     }
   }
   // warp-combined value (every lane holds it)

@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(kThreads) k_map(const In* __restrict__ x, type
   using C = typename S::C;
   constexpr int V = S::kVec;
   constexpr int kOut16 = V * (int)sizeof(C) / 16;  // 16-byte output chunks per input vector
-  const F f = MakeMap<F>::make(P);
+  const auto f = make_kernel_map<F>(P);
   const int64_t tid = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * kThreads;
   int64_t done = 0;

@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const In* __restrict__ x, i
   using A = Acc<C>;
   using Partial = typename A::Partial;
   constexpr int V = S::kVec;
-  const F f = MakeMap<F>::make(P);
+  const auto f = make_kernel_map<F>(P);
   A acc;
 
   const int64_t nvec = (n - head) / V;
@@ -43,13 +43,12 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const In* __restrict__ x, i
       uint4 raw[kUnroll];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) raw[u] = ld_stream(xv + g + u * kThreads + threadIdx.x);
+      C v[kUnroll * V];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        C v[V];
-        S::unpack(raw[u], v);
-        map_vec<V>(f, v);
-        acc.template add_vec<V>(v);
-      }
+      for (int u = 0; u < kUnroll; ++u) S::unpack(raw[u], v + u * V);
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) map_vec<V>(f, v + u * V);
+      acc.template add_vec<kUnroll * V>(v);
     } else {
       for (int u = 0; u < kUnroll; ++u) {
         const int64_t vi = g + u * kThreads + threadIdx.x;

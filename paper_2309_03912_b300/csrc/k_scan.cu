@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) k_scan(const In* __restrict__ x, typ
   __syncthreads();
   const int64_t tile = s_tile;
 
-  const F f = MakeMap<F>::make(P);
+  const auto f = make_kernel_map<F>(P);
   const int64_t base = tile * kTile + (int64_t)tid * kItems;
   C v[kItems];
   if (vec_ok && base + kItems <= n) {

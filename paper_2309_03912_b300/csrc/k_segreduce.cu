@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
   bool wrote_head = false, wrote_tail = false;
 
   if (active) {
-    const F f = MakeMap<F>::make(P);
+    const auto f = make_kernel_map<F>(P);
     const int64_t i0 = warp_lower_bound(off, nseg, a, lane);
     int64_t s = (i0 <= nseg && __ldg(off + i0) == a) ? i0 : i0 - 1;
     if (s < 0) s = 0;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
         break;
       }
       const int64_t pa = imax(lo_s, a), pb = imin(hi_s, b);
-      const Acc<float> acc = warp_reduce_range<In, F>(x, pa, pb, x_aligned, f, lane, b);
+      const Acc<float> acc = warp_reduce_range<In>(x, pa, pb, x_aligned, f, lane, b);
       const Acc<float>::W w = acc.warp();
       const bool head_open = lo_s < a, tail_open = hi_s > b;
       if (lane == 0) {
@@ -161,31 +161,62 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
 
 // ---------------------------------------------------------------------------
 // The same walk with the loads decoupled from the arithmetic (16-byte aligned
-// x): every warp streams its range through a private ring of kStages chunks in
-// shared memory, filled by TMA bulk copies (one lane issues them, an mbarrier
-// per stage tracks the bytes), so kStages - 1 chunks of 2 KiB per warp are in
-// flight while the warp maps and accumulates the current one.  Segment
-// boundaries are handled inside a chunk: the common case (the chunk lies in one
-// segment) accumulates whole vectors; a chunk holding boundaries makes one
-// predicated pass per boundary and emits each finished segment.
+// x): every warp streams its range through a private ring of stages in shared
+// memory, filled by TMA bulk copies (one lane issues them, an mbarrier per
+// stage tracks the bytes), so all but one stage are in flight while the warp
+// maps and accumulates the current one.  A chunk (one stage) holds 16 elements
+// per lane whatever the storage type: 4 vectors per lane in 2 KiB stages for
+// FP32, 2 vectors per lane in 1 KiB stages for FP16 / BF16.  Segment boundaries
+// are handled inside a chunk: the common case (the chunk lies in one segment)
+// accumulates all 16 values at once; a chunk holding boundaries makes one masked
+// pass per piece and emits each finished segment.
+//
+// Ring size and blocks per SM follow the cost of the map (measured on B300 at
+// 2^28 elements, 65,536 segments): maps of a few instructions per element run
+// best as few warps with deep rings (one block of 8 warps, 16 KiB rings: 90 %
+// of the copy bandwidth), the division-bound maps need every warp the
+// registers allow (three blocks, 8 KiB rings), and Horner polynomials sit in
+// between (two blocks, 8 KiB rings).
 // ---------------------------------------------------------------------------
-constexpr int kStages = 4;
-constexpr int kChunkVec = 128;                          // 16-byte vectors per chunk (4 per lane)
-constexpr int kRingBytes = kStages * kChunkVec * 16;    // per warp
-constexpr int kTmaSmem = kWarps * kRingBytes;           // per block (dynamic)
-constexpr long long kTmaWaitLimit = 1ll << 22;          // mbarrier polls before giving up
+template <class F>
+struct SegShape {  // division-bound maps (rational, Newton) and the rest
+  static constexpr int ring = 8192, blocks = 3;
+};
+template <class T>
+struct SegShape<Identity<T>> {
+  static constexpr int ring = 16384, blocks = 1;
+};
+template <class T>
+struct SegShape<Square<T>> {
+  static constexpr int ring = 16384, blocks = 1;
+};
+template <class T, int D>
+struct SegShape<Horner<T, D>> {
+  static constexpr int ring = 8192, blocks = 2;
+};
+template <class T>
+struct SegShape<HornerN<T>> {
+  static constexpr int ring = 8192, blocks = 2;
+};
+constexpr int kMaxStages = 16;
+constexpr uint64_t kTmaWaitNs = 1000000000ull;         // 1 s for one bulk copy before giving up
 
 template <class In, class F>
-__global__ void __launch_bounds__(kThreads, 3) k_segreduce_tma(const In* __restrict__ x, int64_t n,
+__global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma(const In* __restrict__ x, int64_t n,
                                                             const int64_t* __restrict__ off, int64_t nseg,
                                                             int64_t range, int /*x_aligned: always*/,
                                                             const __grid_constant__ MapParams P, RedOut out,
                                                             WsHeader* hdr, SegSlot* slots) {
   using S = Storage<In>;
   constexpr int V = S::kVec;
-  constexpr int E = 4 * V;  // elements per lane per chunk
+  constexpr int E = 16;                      // elements per lane per chunk
+  constexpr int kU = E / V;                  // vectors per lane per chunk
+  constexpr int kChunkVec = 32 * kU;         // 16-byte vectors per chunk
+  constexpr int kRingBytes = SegShape<F>::ring;  // per warp
+  constexpr int kStages = kRingBytes / (kChunkVec * 16);
+  static_assert(kStages >= 2 && kStages <= kMaxStages, "ring layout");
   extern __shared__ __align__(128) uint4 ring_all[];
-  __shared__ __align__(8) uint64_t bars[kWarps][kStages];
+  __shared__ __align__(8) uint64_t bars[kWarps][kMaxStages];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
   const int64_t a = gw * range;
@@ -214,7 +245,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_segreduce_tma(const In* __restr
     if (lane == 0)
       for (int64_t k = 0; k < imin<int64_t>(kStages, nchunks); ++k) issue(k);
 
-    const F f = MakeMap<F>::make(P);
+    const auto f = make_kernel_map<F>(P);
     const int64_t i0 = warp_lower_bound(off, nseg, a, lane);
     int64_t s = (i0 <= nseg && __ldg(off + i0) == a) ? i0 : i0 - 1;
     if (s < 0) s = 0;
@@ -252,49 +283,28 @@ __global__ void __launch_bounds__(kThreads, 3) k_segreduce_tma(const In* __restr
       acc = Acc<float>();
     };
     auto advance = [&]() { return ++s < nseg && bounds(); };
-    // one chunk: vectors [v0, v0 + cnt) of x, staged in ring stage st
+    // one chunk: vectors [v0, v0 + cnt) of x, staged in ring stage st.  Every lane maps
+    // its kU vectors once; a chunk inside one segment is accumulated whole, any other
+    // (segment boundaries inside it, or a short last chunk) by one masked pass per
+    // piece of a segment, on chunk-relative element positions.
     auto chunk = [&](int st, int64_t v0, int cnt) -> bool {
       const int64_t ca = v0 * V, cb = (v0 + cnt) * V;
       const uint4* src = ring + st * kChunkVec;
-      if (hi_s >= cb && cnt == kChunkVec) {  // common case: a full chunk inside segment s
-        float e[4 * V];
+      float e[E];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) S::unpack(src[u * 32 + lane], e + u * V);
+      for (int u = 0; u < kU; ++u) S::unpack(src[u * 32 + lane], e + u * V);  // stale past cnt: masked
 #pragma unroll
-        for (int u = 0; u < 4; ++u) map_vec<V>(f, e + u * V);  // independent chains interleave
-        acc.template add_vec<4 * V>(e);
+      for (int u = 0; u < kU; ++u) map_vec<V>(f, e + u * V);  // independent chains interleave
+      if (hi_s >= cb && cnt == kChunkVec) {
+        acc.template add_vec<E>(e);
         return true;
       }
-      if (hi_s >= cb) {  // a partial chunk inside segment s
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = u * 32 + lane;
-          if (j < cnt) {
-            float e[V];
-            S::unpack(src[j], e);
-            map_vec<V>(f, e);
-            acc.template add_vec<V>(e);
-          }
-        }
-        return true;
-      }
-      // boundaries inside the chunk: one predicated pass per segment piece, re-reading
-      // the stage; indices are chunk-relative
-      int lo = 0;
+      int lo = (int)imax<int64_t>(lo_s - ca, 0);
       while (true) {
         const int end = (int)(imin(hi_s, cb) - ca);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int j = u * 32 + lane, e0 = j * V;
-          if (j < cnt && e0 + V > lo && e0 < end) {
-            float e[V];
-            S::unpack(src[j], e);
-            map_vec<V>(f, e);
-#pragma unroll
-            for (int q = 0; q < V; ++q)
-              if (e0 + q >= lo && e0 + q < end) acc.add(e[q]);
-          }
-        }
+        const int base = lane * V - lo;
+        const unsigned len = (unsigned)(end - lo);
+        acc.template add_if<E>(e, [&](int i) { return (unsigned)(base + (i / V) * 32 * V + i % V) < len; });
         if (hi_s > cb) return true;
         finish();
         if (!advance()) return false;
@@ -307,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_segreduce_tma(const In* __restr
     bool consumed = false;  // whether chunk k (where the loop stopped) was taken from the ring
     for (; k < nchunks && ok; ++k) {
       const int st = (int)(k % kStages);
-      if (!mbar_wait_bounded(bar0 + 8 * st, (uint32_t)((k / kStages) & 1), kTmaWaitLimit)) {
+      if (!mbar_wait_until(bar0 + 8 * st, (uint32_t)((k / kStages) & 1), kTmaWaitNs)) {
         if (lane == 0) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)gw);
         ok = false;
         consumed = false;
@@ -382,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_segreduce_tma(const In* __restr
       const int64_t from = consumed ? k + 1 : k;
       const int64_t to = imin<int64_t>(nchunks, k + kStages);
       for (int64_t j = from; j < to; ++j)
-        mbar_wait_bounded(bar0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), kTmaWaitLimit);
+        mbar_wait_until(bar0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), kTmaWaitNs);
     }
   }
   if (lane == 0) {
@@ -410,7 +420,7 @@ tr_status launch_segreduce(const MapParams& P, const void* x, tr_dtype xt, int64
     constexpr int V = Storage<In>::kVec;
     const bool tma = x_aligned && n > 0;
     auto kern = tma ? k_segreduce_tma<In, F> : k_segreduce<In, F>;
-    const size_t smem = tma ? (size_t)kTmaSmem : 0;
+    const size_t smem = tma ? (size_t)kWarps * SegShape<F>::ring : 0;
     if (tma) {
       static bool attr_set = false;  // per instantiation
       if (!attr_set) {

@@ -28,7 +28,7 @@ namespace tr {
 // bit-identical to two scalar fmas); elsewhere the scalar form is used.  The
 // signature is the same in every pass (the paper's Sec. 2.4 rule); only the
 // body differs.
-#if defined(__CUDA_ARCH__)
+#if defined(__CUDACC__)  // device helpers: declared in both nvcc passes, used in device code
 __device__ __forceinline__ unsigned long long pack_f32x2(float lo, float hi) {
   unsigned long long r;
   asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
@@ -41,6 +41,11 @@ __device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a, un
                                                          unsigned long long c) {
   unsigned long long d;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add_f32x2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
   return d;
 }
 #endif

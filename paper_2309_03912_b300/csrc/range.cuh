@@ -40,13 +40,12 @@ __device__ __forceinline__ Acc<float> warp_reduce_range(const In* __restrict__ x
     uint4 raw[kRangeUnroll];
 #pragma unroll
     for (int u = 0; u < kRangeUnroll; ++u) raw[u] = ld_stream(xv + v + 32 * u);
+    float e[kRangeUnroll * V];
 #pragma unroll
-    for (int u = 0; u < kRangeUnroll; ++u) {
-      float e[V];
-      S::unpack(raw[u], e);
-      map_vec<V>(f, e);
-      acc.template add_vec<V>(e);
-    }
+    for (int u = 0; u < kRangeUnroll; ++u) S::unpack(raw[u], e + u * V);
+#pragma unroll
+    for (int u = 0; u < kRangeUnroll; ++u) map_vec<V>(f, e + u * V);
+    acc.template add_vec<kRangeUnroll * V>(e);
   }
   for (; v < vb; v += 32) {
     float e[V];
