@@ -7,18 +7,15 @@
 //   * a thread owns kItems contiguous elements (128-bit loads) and keeps only
 //     the mapped values in registers; warps scan lane totals with shuffles and
 //     the block combines warp totals in shared memory;
-//   * the tile publishes its aggregate (flag A), then the whole block looks
-//     back over kThreads predecessors per round (one flag per thread), summing
-//     aggregates until it meets an inclusive prefix (flag P), and publishes its
-//     own inclusive prefix.  With hundreds of tiles in flight the nearest P is
-//     usually several hundred tiles back, so a block-wide window takes one or
-//     two rounds where a single warp would need tens;
+//   * the tile publishes its aggregate (flag A), then warp 0 looks back over
+//     32 predecessors per round, summing aggregates until it meets an
+//     inclusive prefix (flag P), and publishes its own inclusive prefix.  A
+//     32-bit carry shares one 64-bit status word with its flag (one relaxed
+//     load, no fence); a 64-bit carry sits beside a flag released after it;
 //   * every wait is bounded by a %globaltimer deadline and an abort word: on
 //     expiry the block records TR_ERR_TIMEOUT and finishes instead of hanging.
-// Each call clears the tile flags and the tile counter with two memsets on
-// the stream (graph-capturable) before the kernel.  Predecessor flags are
-// polled with relaxed loads; one acquire fence per thread and round orders the
-// reads of the values behind them.
+// Each call clears the tile flags / status words and the tile counter with two
+// memsets on the stream (graph-capturable) before the kernel.
 //
 // Arithmetic: u32 wraps modulo 2^32; u32 -> u64 is exact; float scans keep
 // float-float (hi, lo) pairs inside a tile, FP64 between tiles, and round each
@@ -93,134 +90,139 @@ __device__ __forceinline__ typename Op::Carry warp_sum_carry(typename Op::Carry 
 }
 
 struct ScanWs {
-  uint32_t* flags;
-  void* agg;
-  void* incl;
+  uint32_t* flags;          // 64-bit carries: flag per tile (A or P), released after the value
+  void* agg;                // 64-bit carries: tile aggregates; 32-bit carries: packed status words
+  void* incl;               // 64-bit carries: inclusive prefixes
 };
 
-// Decoupled look-back by the whole block for `tile` (aggregate already known):
-// publishes A, then scans kThreads predecessors per round (one flag per
-// thread) until an inclusive prefix P bounds the sum, publishes its own P and
-// returns the exclusive prefix (the same value in every thread).  Every wait
-// is bounded by `deadline` and the abort word.
+// A 32-bit carry travels with its flag in one 64-bit status word (value in the
+// high half, flag in the low bits), so one relaxed load sees both and no fence
+// is needed; wider carries use a flag released after a separate value.
 template <class Op>
-struct LookbackSmem {
-  typename Op::Carry red[kWarps];
-  int first[kWarps];
-};
+constexpr bool kPackedStatus = sizeof(typename Op::Carry) == 4;
 
 template <class Op>
-__device__ __forceinline__ typename Op::Carry block_lookback(int64_t tile, typename Op::Carry aggregate, ScanWs ws,
-                                                             WsHeader* hdr, uint64_t timeout_ns, bool stall,
-                                                             LookbackSmem<Op>& sm) {
+__device__ __forceinline__ void publish(ScanWs ws, int64_t tile, uint32_t flag, typename Op::Carry v) {
+  if constexpr (kPackedStatus<Op>) {
+    st_relaxed_u64(static_cast<unsigned long long*>(ws.agg) + tile, ((unsigned long long)v << 32) | flag);
+  } else {
+    static_cast<typename Op::Carry*>(flag == kFlagP ? ws.incl : ws.agg)[tile] = v;
+    st_release_u32(&ws.flags[tile], flag);
+  }
+}
+
+// Decoupled look-back for `tile` by one warp (the caller's warp 0): publishes
+// the aggregate (flag A), then reads the 32 nearest unread predecessors per
+// round, summing aggregates until an inclusive prefix (flag P) bounds the sum,
+// and publishes its own inclusive prefix.  Returns the exclusive prefix in
+// every lane; sets `gave_up` (and the status word) when a wait runs past the
+// deadline or another block has aborted.
+template <class Op>
+__device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typename Op::Carry aggregate, ScanWs ws,
+                                                            WsHeader* hdr, uint64_t timeout_ns, bool stall, int lane,
+                                                            bool& gave_up) {
   using Carry = typename Op::Carry;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  Carry* agg = static_cast<Carry*>(ws.agg);
-  Carry* incl = static_cast<Carry*>(ws.incl);
   Carry excl = Carry(0);
+  gave_up = false;
   if (tile == 0) {
-    if (tid == 0 && !stall) {
-      incl[0] = aggregate;
-      st_release_u32(&ws.flags[0], kFlagP);
-    }
+    if (lane == 0 && !stall) publish<Op>(ws, 0, kFlagP, aggregate);
     return excl;
   }
-  if (tid == 0 && !stall) {
-    agg[tile] = aggregate;
-    st_release_u32(&ws.flags[tile], kFlagA);
-  }
+  if (lane == 0 && !stall) publish<Op>(ws, tile, kFlagA, aggregate);
   const uint64_t deadline = globaltimer_ns() + timeout_ns;
   int64_t pos = tile - 1;
   while (true) {
-    const int64_t idx = pos - tid;
+    const int64_t idx = pos - lane;
     uint32_t st = kFlagP;  // before tile 0: an inclusive prefix of 0
-    int gave_up = 0;
-    if (idx >= 0) {  // relaxed polling; one acquire fence once the flag is seen
+    Carry val = Carry(0);
+    int stop = 0;
+    if (idx >= 0) {
       for (int polls = 0;; ++polls) {
-        st = ld_relaxed_u32(&ws.flags[idx]) & 3u;
+        if constexpr (kPackedStatus<Op>) {
+          const unsigned long long w = ld_relaxed_u64(static_cast<const unsigned long long*>(ws.agg) + idx);
+          st = (uint32_t)w & 3u;
+          val = (Carry)(w >> 32);
+        } else {
+          st = ld_relaxed_u32(&ws.flags[idx]) & 3u;
+        }
         if (st) break;
         if ((polls & 15) == 15 && (globaltimer_ns() > deadline || ld_relaxed_u32(&hdr->abort) != 0u)) {
-          gave_up = 1;
+          stop = 1;
           break;
         }
-        if (polls > 8) __nanosleep(20);
       }
-      fence_acq_rel_gpu();
+      if constexpr (!kPackedStatus<Op>) {
+        if (st) {
+          fence_acq_rel_gpu();  // orders the value read after the flag
+          val = static_cast<const Carry*>(st == kFlagP ? ws.incl : ws.agg)[idx];
+        }
+      }
     }
-    if (__syncthreads_or(gave_up)) {
-      if (tid == 0 && !ld_relaxed_u32(&hdr->abort)) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)tile);
-      break;
+    if (__any_sync(kFull, stop)) {
+      if (lane == 0 && !ld_relaxed_u32(&hdr->abort)) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)tile);
+      gave_up = true;
+      return excl;
     }
-    Carry val = Carry(0);
-    if (idx >= 0) val = (st == kFlagP) ? incl[idx] : agg[idx];
     const unsigned pm = __ballot_sync(kFull, st == kFlagP);
-    if (lane == 0) sm.first[wid] = pm ? __ffs(pm) - 1 : 32;
-    __syncthreads();
-    int first = kThreads;  // nearest predecessor holding an inclusive prefix (block-wide)
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w)
-      if (first == kThreads && sm.first[w] < 32) first = w * 32 + sm.first[w];
-    const Carry part = warp_sum_carry<Op>(tid <= first ? val : Carry(0));
-    if (lane == 0) sm.red[wid] = part;
-    __syncthreads();
-    Carry round = Carry(0);
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) round = Op::cadd(round, sm.red[w]);  // fixed order
-    excl = Op::cadd(excl, round);
-    __syncthreads();  // sm is reused next round
-    if (first < kThreads) break;
-    pos -= kThreads;
+    const int first = pm ? __ffs(pm) - 1 : 32;  // nearest predecessor holding an inclusive prefix
+    excl = Op::cadd(excl, warp_sum_carry<Op>(lane <= first ? val : Carry(0)));
+    if (pm) break;
+    pos -= 32;
   }
-  if (tid == 0 && !stall) {
-    incl[tile] = Op::cadd(excl, aggregate);
-    st_release_u32(&ws.flags[tile], kFlagP);
-  }
+  if (lane == 0 && !stall) publish<Op>(ws, tile, kFlagP, Op::cadd(excl, aggregate));
   return excl;
 }
 
-// The thread's kItems outputs: its running prefix on top of everything before it.
+// Shape of a scan launch by map cost: cheap maps keep six tiles per SM; maps
+// with many coefficients or divisions need the registers of four.
+template <class F>
+struct ScanShape {
+  static constexpr int blocks = 6;
+};
+template <class T, int DP, int DQ>
+struct ScanShape<Rational<T, DP, DQ>> {
+  static constexpr int blocks = 4;
+};
+template <class T>
+struct ScanShape<RationalN<T>> {
+  static constexpr int blocks = 4;
+};
+template <class T, int I>
+struct ScanShape<NewtonCbrt<T, I>> {
+  static constexpr int blocks = 4;
+};
+template <class T>
+struct ScanShape<HornerN<T>> {
+  static constexpr int blocks = 4;
+};
+
+// One item into a running in-tile value (TwoSum into (hi, lo) for floats).
 template <class Op, class C>
-__device__ __forceinline__ void scan_outputs(const C* v, typename Op::Carry prefix, typename Op::T warp_off,
-                                             typename Op::T excl_lane, typename Op::Out* o) {
-  using T = typename Op::T;
+__device__ __forceinline__ void run_add(typename Op::T& run, C v) {
   if constexpr (std::is_same<Op, OpF32>::value) {
-    FF run = ff_add(ff_add(ff_from_double(prefix), warp_off), excl_lane);
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      float sm, e;
-      two_sum(run.hi, v[i], sm, e);
-      run.hi = sm;
-      run.lo += e;
-      o[i] = run.hi + run.lo;  // the compensated prefix, rounded once
-    }
+    float sm, e;
+    two_sum(run.hi, v, sm, e);
+    run.hi = sm;
+    run.lo += e;
   } else {
-    T run = Op::add(Op::add((T)prefix, warp_off), excl_lane);
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      run = Op::add(run, Op::lift(v[i]));
-      o[i] = run;
-    }
+    run = Op::add(run, Op::lift(v));
+  }
+}
+template <class Op>
+__device__ __forceinline__ typename Op::Out run_out(const typename Op::T& run) {
+  if constexpr (std::is_same<Op, OpF32>::value) {
+    return run.hi + run.lo;  // the compensated prefix, rounded once
+  } else {
+    return run;
   }
 }
 
-// Thread totals of the kItems values, warp-scanned; block totals in shared memory.
-template <class Op, class C>
-__device__ __forceinline__ void scan_totals(const C* v, typename Op::T* s_warp, typename Op::T& warp_off,
-                                            typename Op::T& excl_lane, typename Op::T& tile_tot) {
+// Lane totals warp-scanned; block totals in shared memory.
+template <class Op>
+__device__ __forceinline__ void block_totals(typename Op::T acc, typename Op::T* s_warp, typename Op::T& warp_off,
+                                             typename Op::T& excl_lane, typename Op::T& tile_tot) {
   using T = typename Op::T;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  T acc = Op::zero();
-#pragma unroll
-  for (int i = 0; i < kItems; ++i) {
-    if constexpr (std::is_same<Op, OpF32>::value) {  // TwoSum into (hi, lo)
-      float sm, e;
-      two_sum(acc.hi, v[i], sm, e);
-      acc.hi = sm;
-      acc.lo += e;
-    } else {
-      acc = Op::add(acc, Op::lift(v[i]));
-    }
-  }
   const T incl_lane = warp_incl_scan<Op>(acc, lane);
   excl_lane = Op::shfl_up(incl_lane, 1);
   if (lane == 0) excl_lane = Op::zero();
@@ -235,65 +237,127 @@ __device__ __forceinline__ void scan_totals(const C* v, typename Op::T* s_warp, 
   }
 }
 
-template <class Out>
-__device__ __forceinline__ void store_items(Out* y, int64_t base, int64_t n, bool vec, const Out* o) {
-  if (vec && base + kItems <= n) {
-    uint4* yv = reinterpret_cast<uint4*>(y + base);
-    constexpr int kPer = 16 / (int)sizeof(Out);
-#pragma unroll
-    for (int j = 0; j < kItems / kPer; ++j) st_stream(yv + j, pack16(o + j * kPer));
-  } else {
-#pragma unroll
-    for (int i = 0; i < kItems; ++i)
-      if (base + i < n) y[base + i] = o[i];
-  }
-}
+// Plain form: one tile per block, tile ids drawn in launch order.  The tile
+// moves through shared memory in both directions so that every global access
+// is a coalesced 16-byte-per-lane access: lanes load consecutive vectors, map
+// them and scatter the values into per-thread rows (thread t owns the kItems
+// contiguous elements t*kItems...; rows padded to kItems + 1 words, which makes
+// the scatter, the row reads and the final gather free of bank conflicts).
+// No register holds a tile value during the look-back.  After it, each thread
+// scans its row on top of its prefix in place (outputs of 4 bytes) and the
+// block stores the rows back out as coalesced vectors; 8-byte outputs are
+// stored from the thread's registers.
+constexpr int kRow = kItems + 1;  // padded row, in 4-byte words
 
-// Plain form: one tile per block, tile ids drawn in launch order, loads
-// straight to registers (any alignment).
 template <class In, class F, class Op>
-__global__ void __launch_bounds__(kThreads) k_scan(const In* __restrict__ x, typename Op::Out* y, int64_t n, int vec_ok,
-                                                   const __grid_constant__ MapParams P, WsHeader* hdr, ScanWs ws,
-                                                   const typename Op::Out* carry_in, uint64_t timeout_ns,
-                                                   int64_t stall_tile) {
+__global__ void __launch_bounds__(kThreads, ScanShape<F>::blocks)
+    k_scan(const In* __restrict__ x, typename Op::Out* y, int64_t n, int vec_ok, const __grid_constant__ MapParams P,
+           WsHeader* hdr, ScanWs ws, const typename Op::Out* carry_in, uint64_t timeout_ns, int64_t stall_tile) {
   using S = Storage<In>;
   using C = typename S::C;
   using T = typename Op::T;
   using Carry = typename Op::Carry;
   using Out = typename Op::Out;
+  static_assert(sizeof(C) == 4, "4-byte compute values");
   constexpr int V = S::kVec;
-  constexpr int kLoads = kItems / V;
+  constexpr int kVecs = kTile / V;  // input vectors per tile
+  constexpr int kLoads = kVecs / kThreads;
 
   __shared__ uint32_t s_tile;
   __shared__ T s_warp[kWarps];
-  __shared__ LookbackSmem<Op> s_lb;
+  __shared__ Carry s_excl;
+  __shared__ C s_rows[kThreads * kRow];
   const int tid = threadIdx.x;
   if (tid == 0) s_tile = atomicAdd(&hdr->tile_counter, 1u);
   __syncthreads();
   const int64_t tile = s_tile;
 
   const auto f = make_kernel_map<F>(P);
-  const int64_t base = tile * kTile + (int64_t)tid * kItems;
-  C v[kItems];
-  if (vec_ok && base + kItems <= n) {
-    const uint4* xv = reinterpret_cast<const uint4*>(x + base);
+  const int64_t t0 = tile * kTile;
+  const bool full = vec_ok && t0 + kTile <= n;
+  if (full) {
+    const uint4* xv = reinterpret_cast<const uint4*>(x + t0);
     uint4 raw[kLoads];
 #pragma unroll
-    for (int j = 0; j < kLoads; ++j) raw[j] = ld_cached(xv + j);
+    for (int j = 0; j < kLoads; ++j) raw[j] = ld_stream(xv + j * kThreads + tid);
 #pragma unroll
-    for (int j = 0; j < kLoads; ++j) S::unpack(raw[j], v + j * V);
-    map_vec<kItems>(f, v);
+    for (int j = 0; j < kLoads; ++j) {
+      C e[V];
+      S::unpack(raw[j], e);
+      map_vec<V>(f, e);
+      const int p0 = (j * kThreads + tid) * V;
+#pragma unroll
+      for (int q = 0; q < V; ++q) s_rows[((p0 + q) / kItems) * kRow + (p0 + q) % kItems] = e[q];
+    }
   } else {
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) v[i] = (base + i < n) ? f(S::cvt(x[base + i])) : C(0);
+    for (int p = tid; p < kTile; p += kThreads)
+      s_rows[(p / kItems) * kRow + p % kItems] = (t0 + p < n) ? f(S::cvt(x[t0 + p])) : C(0);
   }
+  __syncthreads();
+  C* row = s_rows + tid * kRow;
+  T acc = Op::zero();
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) run_add<Op>(acc, row[i]);
   T warp_off, excl_lane, tile_tot;
-  scan_totals<Op>(v, s_warp, warp_off, excl_lane, tile_tot);
-  const Carry excl = block_lookback<Op>(tile, Op::to_carry(tile_tot), ws, hdr, timeout_ns, tile == stall_tile, s_lb);
-  const Carry prefix = Op::cadd(carry_in ? Carry(*carry_in) : Carry(0), excl);
-  Out o[kItems];
-  scan_outputs<Op>(v, prefix, warp_off, excl_lane, o);
-  store_items(y, base, n, vec_ok, o);
+  block_totals<Op>(acc, s_warp, warp_off, excl_lane, tile_tot);
+  if (tid < 32) {  // warp 0 looks back while the others wait
+    bool gave_up;
+    const Carry e = warp_lookback<Op>(tile, Op::to_carry(tile_tot), ws, hdr, timeout_ns, tile == stall_tile, tid,
+                                      gave_up);
+    if (tid == 0) s_excl = e;
+  }
+  __syncthreads();
+  const Carry prefix = Op::cadd(carry_in ? Carry(*carry_in) : Carry(0), s_excl);
+
+  // the thread's outputs: its running prefix on top of everything before it
+  T run;
+  if constexpr (std::is_same<Op, OpF32>::value) {
+    run = ff_add(ff_add(ff_from_double(prefix), warp_off), excl_lane);
+  } else {
+    run = Op::add(Op::add((T)prefix, warp_off), excl_lane);
+  }
+  if constexpr (sizeof(Out) == 4) {
+    Out* orow = reinterpret_cast<Out*>(row);
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      run_add<Op>(run, row[i]);
+      orow[i] = run_out<Op>(run);  // in place: this thread alone reads and writes its row
+    }
+    __syncthreads();
+    const Out* orows = reinterpret_cast<const Out*>(s_rows);
+    if (full) {
+      uint4* yv = reinterpret_cast<uint4*>(y + t0);
+#pragma unroll
+      for (int j = 0; j < kTile / 4 / kThreads; ++j) {
+        const int p0 = (j * kThreads + tid) * 4;
+        Out o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = orows[((p0 + q) / kItems) * kRow + (p0 + q) % kItems];
+        st_stream(yv + j * kThreads + tid, pack16(o));
+      }
+    } else {
+      for (int p = tid; p < kTile && t0 + p < n; p += kThreads) y[t0 + p] = orows[(p / kItems) * kRow + p % kItems];
+    }
+  } else {
+    const int64_t base = t0 + (int64_t)tid * kItems;
+    constexpr int kPer = 16 / (int)sizeof(Out);
+#pragma unroll
+    for (int g = 0; g < kItems / kPer; ++g) {
+      Out o[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        run_add<Op>(run, row[g * kPer + q]);
+        o[q] = run_out<Op>(run);
+      }
+      if (full) {
+        st_stream(reinterpret_cast<uint4*>(y + base) + g, pack16(o));
+      } else {
+#pragma unroll
+        for (int q = 0; q < kPer; ++q)
+          if (base + g * kPer + q < n) y[base + g * kPer + q] = o[q];
+      }
+    }
+  }
 }
 
 }  // namespace
@@ -317,8 +381,9 @@ tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, t
   cudaStream_t st = stream_of(e);
   WsHeader* hdr = ws_header(e);
   const int64_t stall = e->debug_stall_tile;
-  // every call starts from clear tile flags and a zero tile counter
-  tr_status s = cuda_status(cudaMemsetAsync(ws.flags, 0, (size_t)tiles * 4, st), "cudaMemsetAsync(scan flags)");
+  // every call starts from clear tile flags and status words (one memset over both) and a zero tile counter
+  tr_status s = cuda_status(cudaMemsetAsync(ws.flags, 0, (size_t)(flags_b + tiles * 8), st),
+                            "cudaMemsetAsync(scan flags)");
   if (!s) s = cuda_status(cudaMemsetAsync(&hdr->tile_counter, 0, sizeof(uint32_t), st), "cudaMemsetAsync(counter)");
   if (s) return s;
   auto go = [&](auto op_tag) {
