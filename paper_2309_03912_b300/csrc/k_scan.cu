@@ -4,9 +4,10 @@
 // parallel prefix scan with decoupled look-back", NVR-2016-002):
 //   * each block takes a tile id from an atomic counter (dynamic ids: every
 //     tile's predecessors have already started, so waiting on them ends);
-//   * a thread owns kItems contiguous elements (128-bit loads) and keeps only
-//     the mapped values in registers; warps scan lane totals with shuffles and
-//     the block combines warp totals in shared memory;
+//   * lanes load consecutive 128-bit vectors of the tile (coalesced), map
+//     them and park the values in shared memory, one padded row of kItems
+//     contiguous elements per thread; threads total their rows, warps scan the
+//     totals with shuffles and the block combines warp totals;
 //   * the tile publishes its aggregate (flag A), then warp 0 looks back over
 //     32 predecessors per round, summing aggregates until it meets an
 //     inclusive prefix (flag P), and publishes its own inclusive prefix.  A
@@ -248,6 +249,7 @@ __device__ __forceinline__ void block_totals(typename Op::T acc, typename Op::T*
 // block stores the rows back out as coalesced vectors; 8-byte outputs are
 // stored from the thread's registers.
 constexpr int kRow = kItems + 1;  // padded row, in 4-byte words
+constexpr size_t kRowsBytes = (size_t)kThreads * kRow * 4;  // dynamic shared memory per block
 
 template <class In, class F, class Op>
 __global__ void __launch_bounds__(kThreads, ScanShape<F>::blocks)
@@ -266,7 +268,8 @@ __global__ void __launch_bounds__(kThreads, ScanShape<F>::blocks)
   __shared__ uint32_t s_tile;
   __shared__ T s_warp[kWarps];
   __shared__ Carry s_excl;
-  __shared__ C s_rows[kThreads * kRow];
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  C* s_rows = reinterpret_cast<C*>(s_dyn);  // kThreads * kRow values
   const int tid = threadIdx.x;
   if (tid == 0) s_tile = atomicAdd(&hdr->tile_counter, 1u);
   __syncthreads();
@@ -392,7 +395,16 @@ tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, t
       using In = decltype(in_tag);
       using F = decltype(map_tag);
       using Out = typename Op::Out;
-      k_scan<In, F, Op><<<(unsigned)tiles, kThreads, 0, st>>>(static_cast<const In*>(x), static_cast<Out*>(y), n,
+      auto kern = k_scan<In, F, Op>;
+      static bool attr_set = false;  // per instantiation
+      if (!attr_set) {
+        tr_status a = cuda_status(
+            cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowsBytes),
+            "cudaFuncSetAttribute(k_scan)");
+        if (a) return a;
+        attr_set = true;
+      }
+      kern<<<(unsigned)tiles, kThreads, kRowsBytes, st>>>(static_cast<const In*>(x), static_cast<Out*>(y), n,
                                                               vec_ok, P, hdr, ws, static_cast<const Out*>(carry),
                                                               timeout_ns, stall);
       return launch_status("k_scan");
