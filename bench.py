@@ -46,6 +46,7 @@ WORKLOAD = ("segmented transform-reduce: N=2^28 f32 x~N(0,1), f = rational P/Q d
             "coefficients), 65536 segments with lengths U{1..8192} scaled to N; per segment compensated "
             "sum (f64 out), min, max")
 SEG_SOURCES = ["paper_2309_03912_b300/csrc/k_segreduce.cu", "paper_2309_03912_b300/csrc/accum.cuh",
+               "paper_2309_03912_b300/csrc/range.cuh", "paper_2309_03912_b300/csrc/dispatch.cuh",
                "paper_2309_03912_b300/csrc/common.cuh", "paper_2309_03912_b300/csrc/maps.h"]
 
 
@@ -156,6 +157,17 @@ def profile_traffic(kernel: str, sources: list[str]):
     return None, None, sha
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (every rank gets it); the job's throughput is
+    the units all ranks processed divided by this."""
+    if world == 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_launches(fn, steps, warmup, stream):
     """Device time per call (ms): CUDA events on `stream` between calls."""
     import torch
@@ -246,10 +258,7 @@ def headline(args, rank, world, stream):
         B.tr_check(ex)
         per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
         total_ms = evs[0].elapsed_time(evs[-1])
-        if world > 1:
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, world, "cuda")
 
         # end to end through the public API: pinned host input in, results out, every step
         xh = torch.from_numpy(x).pin_memory()
