@@ -161,7 +161,14 @@ struct NewtonCbrt {
   TR_HD constexpr T operator()(T x) const {
     T y = copysign_one(x);
     const int n = ITERS >= 0 ? ITERS : iters;
-    for (int k = 0; k < n; ++k) y = (T(2) * y + x / (y * y)) / T(3);
+    for (int k = 0; k < n; ++k) {
+      const T s = fma_hd(T(2), y, x / (y * y));  // 2y is exact, so this is RN(2y + x/y^2)
+      if constexpr (std::is_same<T, float>::value) {
+        y = div3_hd(s);  // = RN(s / 3), division-free
+      } else {
+        y = s / T(3);
+      }
+    }
     return y;
   }
 };

@@ -8,7 +8,9 @@
 //   receives FP64 results.
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "maps.h"
@@ -67,7 +69,36 @@ static void run_float(const char* kind, int iters, const std::vector<T>& p, cons
   }
 }
 
+// div3_hd against the IEEE quotient s / 3.0f for all 2^32 bit patterns
+// (NaN inputs: both results NaN).  Prints the number of mismatches.
+static int check_div3_all() {
+  const unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+  std::vector<unsigned long long> bad(nt, 0);
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t)
+    th.emplace_back([t, nt, &bad] {
+      const uint64_t lo = (1ull << 32) * t / nt, hi = (1ull << 32) * (t + 1) / nt;
+      for (uint64_t u = lo; u < hi; ++u) {
+        float s;
+        const uint32_t b = (uint32_t)u;
+        memcpy(&s, &b, 4);
+        volatile float three = 3.0f;
+        const float want = s / three, got = div3_hd(s);
+        uint32_t bw, bg;
+        memcpy(&bw, &want, 4);
+        memcpy(&bg, &got, 4);
+        if (bw != bg && !(want != want && got != got)) ++bad[t];
+      }
+    });
+  for (auto& x : th) x.join();
+  unsigned long long total = 0;
+  for (auto v : bad) total += v;
+  printf("%llu\n", total);
+  return total ? 5 : 0;
+}
+
 int main(int argc, char** argv) {
+  if (argc == 2 && !strcmp(argv[1], "div3")) return check_div3_all();
   if (argc < 7) return 2;
   const char* kind = argv[1];
   const bool dbl = argv[2][0] == 'd';

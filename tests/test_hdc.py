@@ -24,7 +24,7 @@ CSRC = os.path.join(ROOT, "paper_2309_03912_b300", "csrc")
 
 def build_host_check() -> str:
     out = os.path.join(tempfile.mkdtemp(), "hdc_host_check")
-    subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-I" + CSRC,
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-pthread", "-I" + CSRC,
                            os.path.join(ROOT, "tests", "hdc_host_check.cpp"), "-o", out])
     return out
 
@@ -81,3 +81,11 @@ def test_host_mixers_equal_oracle(orc, host_bin, kind):
     x = np.random.default_rng(4).integers(0, 1 << 32, 5000, dtype=np.uint64).astype(np.uint32)
     y = host_eval(host_bin, {"kind": kind}, x.astype(np.float64), "d").astype(np.uint64).astype(np.uint32)
     assert np.array_equal(y, orc.map_values(orc.MapSpec(kind), x))
+
+
+def test_div3_is_the_ieee_quotient_for_every_float(host_bin):
+    """The division-free s / 3 of the FP32 Newton map (Markstein correction
+    after a multiply by RN(1/3)) equals the IEEE quotient s / 3.0f bit for
+    bit over all 2^32 inputs, subnormals, infinities and zeros included."""
+    r = subprocess.run([host_bin, "div3"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip() == "0", (r.returncode, r.stdout, r.stderr)
