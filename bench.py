@@ -62,6 +62,8 @@ def parse():
                                               "(scan_u32, scan_f32, reduce_f64, mixers_2^20, batched, vandermonde, f16); "
                                               "skips the headline")
     p.add_argument("--config-log2", type=int, default=28, help="log2 size of the 2^28 scan configurations")
+    p.add_argument("--vander-log2-m", type=int, default=20,
+                   help="log2 of the points of the Vandermonde configuration (smaller only for profiler captures)")
     p.add_argument("--head-n", type=int, default=N_HEAD,
                    help="elements of the headline workload (segments scale with it); smaller sizes are "
                         "for profiler captures only")
@@ -392,7 +394,7 @@ def other_configs(args, stream, hbm_peak):
     if want('vandermonde'):
         # 4096 polynomials of degree 31 at 2^20 points: Y = V(x) C (16 GiB of FP32 output), split-BF16 on
         # the tensor cores against plain FP32 Horner on the CUDA cores
-        x, C = I.vandermonde()
+        x, C = I.vandermonde(1 << args.vander_log2_m)
         xd, Cd = torch.from_numpy(x).cuda(), torch.from_numpy(C).cuda()
         m, npoly = x.size, C.shape[1]
         y = torch.empty((m, npoly), dtype=torch.float32, device="cuda")
@@ -404,11 +406,12 @@ def other_configs(args, stream, hbm_peak):
         B.tr_check(exv)
         flops = 2.0 * m * 32 * npoly
         nbytes = m * npoly * 4 + m * 4 + C.nbytes
-        record("vandermonde_bf16x3_2^20x32x4096", ms_tc, m * npoly, nbytes, 1,
+        vtag = f"2^{args.vander_log2_m}x32x4096"
+        record(f"vandermonde_bf16x3_{vtag}", ms_tc, m * npoly, nbytes, 1,
                {"bound": "hbm (output write)", "tflops_algorithmic": round(flops / (ms_tc * 1e-3) / 1e12, 1),
                 "tflops_tensor_executed": round(3 * flops / (ms_tc * 1e-3) / 1e12, 1),
                 "fp32_horner_ms": round(ms_32, 4), "speedup_vs_fp32_horner": round(ms_32 / ms_tc, 3)})
-        record("vandermonde_fp32_horner_2^20x32x4096", ms_32, m * npoly, nbytes, 1,
+        record(f"vandermonde_fp32_horner_{vtag}", ms_32, m * npoly, nbytes, 1,
                {"bound": "fp32 fma pipe / hbm", "tflops": round(flops / (ms_32 * 1e-3) / 1e12, 1)})
         del y, xd, Cd
 
