@@ -257,7 +257,7 @@ tr_status tr_vandermonde(const float* d_x, int64_t m, const float* d_coef, int32
  * The paper has no counterpart to this entry point.
  *
  * The scratch lives in one fixed device array inside the library (about
- * 320 KiB, reserved on every GPU that loads the library and held until the
+ * 1 MiB, reserved on every GPU that loads the library and held until the
  * process exits), so n is limited to 2^26 elements; larger n is rejected with
  * TR_ERR_INVALID_ARG and a message naming the limit.  The call makes no
  * allocation of any kind.  Its first call on a device looks up the array's

@@ -9,14 +9,16 @@
 //     contiguous elements per thread; threads total their rows, warps scan the
 //     totals with shuffles and the block combines warp totals;
 //   * the tile publishes its aggregate (flag A), then warp 0 looks back over
-//     32 predecessors per round, summing aggregates until it meets an
-//     inclusive prefix (flag P), and publishes its own inclusive prefix.  A
-//     32-bit carry shares one 64-bit status word with its flag (one relaxed
-//     load, no fence); a 64-bit carry sits beside a flag released after it;
+//     32 (32-bit carries) or 128 (64-bit carries) predecessors per round,
+//     summing aggregates until it meets an inclusive prefix (flag P), and
+//     publishes its own inclusive prefix.  Each tile's state has its own
+//     128-byte line; a 32-bit carry shares one 64-bit status word with its
+//     flag (one relaxed load, no fence), a 64-bit carry sits beside a flag
+//     released after it;
 //   * every wait is bounded by a %globaltimer deadline and an abort word: on
 //     expiry the block records TR_ERR_TIMEOUT and finishes instead of hanging.
-// Each call clears the tile flags / status words and the tile counter with two
-// memsets on the stream (graph-capturable) before the kernel.
+// Each call clears the look-back lines and the tile counter with two memsets
+// on the stream (graph-capturable) before the kernel.
 //
 // Arithmetic: u32 wraps modulo 2^32; u32 -> u64 is exact; float scans keep
 // float-float (hi, lo) pairs inside a tile, FP64 between tiles, and round each
@@ -90,31 +92,40 @@ __device__ __forceinline__ typename Op::Carry warp_sum_carry(typename Op::Carry 
   return v;
 }
 
+// Look-back state: one 128-byte line per tile, so that the polls of hundreds
+// of waiting tiles spread over many L2 lines instead of hammering a few (with
+// the state packed contiguously the polls contended for a handful of lines and
+// the u32 scan ran 25 % slower).  A 32-bit carry travels with its flag in one
+// 64-bit status word at the start of the line (value in the high half, flag in
+// the low bits), so one relaxed load sees both and no fence is needed; a
+// 64-bit carry sits in the same line (aggregate at byte 8, inclusive prefix at
+// byte 16) and its flag (byte 0) is released after it.
+constexpr int kLineBytes = 128;
 struct ScanWs {
-  uint32_t* flags;          // 64-bit carries: flag per tile (A or P), released after the value
-  void* agg;                // 64-bit carries: tile aggregates; 32-bit carries: packed status words
-  void* incl;               // 64-bit carries: inclusive prefixes
+  unsigned char* lines;  // tiles x kLineBytes
 };
 
-// A 32-bit carry travels with its flag in one 64-bit status word (value in the
-// high half, flag in the low bits), so one relaxed load sees both and no fence
-// is needed; wider carries use a flag released after a separate value.
 template <class Op>
 constexpr bool kPackedStatus = sizeof(typename Op::Carry) == 4;
 
+__device__ __forceinline__ unsigned char* status_line(ScanWs ws, int64_t tile) {
+  return ws.lines + tile * kLineBytes;
+}
+
 template <class Op>
 __device__ __forceinline__ void publish(ScanWs ws, int64_t tile, uint32_t flag, typename Op::Carry v) {
+  unsigned char* line = status_line(ws, tile);
   if constexpr (kPackedStatus<Op>) {
-    st_relaxed_u64(static_cast<unsigned long long*>(ws.agg) + tile, ((unsigned long long)v << 32) | flag);
+    st_relaxed_u64(reinterpret_cast<unsigned long long*>(line), ((unsigned long long)v << 32) | flag);
   } else {
-    static_cast<typename Op::Carry*>(flag == kFlagP ? ws.incl : ws.agg)[tile] = v;
-    st_release_u32(&ws.flags[tile], flag);
+    *reinterpret_cast<typename Op::Carry*>(line + (flag == kFlagP ? 16 : 8)) = v;
+    st_release_u32(reinterpret_cast<uint32_t*>(line), flag);
   }
 }
 
 // Decoupled look-back for `tile` by one warp (the caller's warp 0): publishes
-// the aggregate (flag A), then reads the 32 nearest unread predecessors per
-// round, summing aggregates until an inclusive prefix (flag P) bounds the sum,
+// the aggregate (flag A), then reads the nearest unread predecessors (32 or
+// 128 per round), summing aggregates until an inclusive prefix (flag P) bounds the sum,
 // and publishes its own inclusive prefix.  Returns the exclusive prefix in
 // every lane; sets `gave_up` (and the status word) when a wait runs past the
 // deadline or another block has aborted.
@@ -123,6 +134,10 @@ __device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typena
                                                             WsHeader* hdr, uint64_t timeout_ns, bool stall, int lane,
                                                             bool& gave_up) {
   using Carry = typename Op::Carry;
+  // predecessors read per lane and round: one for 32-bit carries, four (a
+  // 128-tile window) for 64-bit carries, whose rounds cost a fence and a
+  // second load (measured on B300: the f32 scan gains 6 %, the u32 scan none)
+  constexpr int kSlots = kPackedStatus<Op> ? 1 : 4;
   Carry excl = Carry(0);
   gave_up = false;
   if (tile == 0) {
@@ -133,30 +148,36 @@ __device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typena
   const uint64_t deadline = globaltimer_ns() + timeout_ns;
   int64_t pos = tile - 1;
   while (true) {
-    const int64_t idx = pos - lane;
-    uint32_t st = kFlagP;  // before tile 0: an inclusive prefix of 0
-    Carry val = Carry(0);
+    // slot m of lane l reads the predecessor at distance 32 m + l from pos
+    uint32_t st[kSlots];
+    Carry val[kSlots];
     int stop = 0;
-    if (idx >= 0) {
-      for (int polls = 0;; ++polls) {
-        if constexpr (kPackedStatus<Op>) {
-          const unsigned long long w = ld_relaxed_u64(static_cast<const unsigned long long*>(ws.agg) + idx);
-          st = (uint32_t)w & 3u;
-          val = (Carry)(w >> 32);
-        } else {
-          st = ld_relaxed_u32(&ws.flags[idx]) & 3u;
-        }
-        if (st) break;
-        if ((polls & 15) == 15 && (globaltimer_ns() > deadline || ld_relaxed_u32(&hdr->abort) != 0u)) {
-          stop = 1;
-          break;
+#pragma unroll
+    for (int m = 0; m < kSlots; ++m) {
+      st[m] = kFlagP;  // before tile 0: an inclusive prefix of 0
+      val[m] = Carry(0);
+    }
+    for (int polls = 0;; ++polls) {  // the window's loads are issued together; waits are bounded
+      bool pending = false;
+#pragma unroll
+      for (int m = 0; m < kSlots; ++m) {
+        const int64_t idx = pos - 32 * m - lane;
+        if (idx >= 0 && (polls == 0 || st[m] == 0)) {
+          const unsigned char* line = status_line(ws, idx);
+          if constexpr (kPackedStatus<Op>) {
+            const unsigned long long w = ld_relaxed_u64(reinterpret_cast<const unsigned long long*>(line));
+            st[m] = (uint32_t)w & 3u;
+            val[m] = (Carry)(w >> 32);
+          } else {
+            st[m] = ld_relaxed_u32(reinterpret_cast<const uint32_t*>(line)) & 3u;
+          }
+          pending |= st[m] == 0;
         }
       }
-      if constexpr (!kPackedStatus<Op>) {
-        if (st) {
-          fence_acq_rel_gpu();  // orders the value read after the flag
-          val = static_cast<const Carry*>(st == kFlagP ? ws.incl : ws.agg)[idx];
-        }
+      if (!pending) break;
+      if ((polls & 15) == 15 && (globaltimer_ns() > deadline || ld_relaxed_u32(&hdr->abort) != 0u)) {
+        stop = 1;
+        break;
       }
     }
     if (__any_sync(kFull, stop)) {
@@ -164,11 +185,28 @@ __device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typena
       gave_up = true;
       return excl;
     }
-    const unsigned pm = __ballot_sync(kFull, st == kFlagP);
-    const int first = pm ? __ffs(pm) - 1 : 32;  // nearest predecessor holding an inclusive prefix
-    excl = Op::cadd(excl, warp_sum_carry<Op>(lane <= first ? val : Carry(0)));
-    if (pm) break;
-    pos -= 32;
+    if constexpr (!kPackedStatus<Op>) {
+      fence_acq_rel_gpu();  // orders the value reads after the flags
+#pragma unroll
+      for (int m = 0; m < kSlots; ++m) {
+        const int64_t idx = pos - 32 * m - lane;
+        if (idx >= 0) val[m] = *reinterpret_cast<const Carry*>(status_line(ws, idx) + (st[m] == kFlagP ? 16 : 8));
+      }
+    }
+    // the nearest predecessor holding an inclusive prefix: everything up to it is summed
+    int first = 32 * kSlots;
+#pragma unroll
+    for (int m = kSlots - 1; m >= 0; --m) {
+      const unsigned pm = __ballot_sync(kFull, st[m] == kFlagP);
+      if (pm) first = 32 * m + __ffs(pm) - 1;
+    }
+    Carry part = Carry(0);
+#pragma unroll
+    for (int m = 0; m < kSlots; ++m)
+      if (32 * m + lane <= first) part = Op::cadd(part, val[m]);
+    excl = Op::cadd(excl, warp_sum_carry<Op>(part));
+    if (first < 32 * kSlots) break;
+    pos -= 32 * kSlots;
   }
   if (lane == 0 && !stall) publish<Op>(ws, tile, kFlagP, Op::cadd(excl, aggregate));
   return excl;
@@ -367,26 +405,22 @@ __global__ void __launch_bounds__(kThreads, ScanShape<F>::blocks)
 
 size_t scan_ws_bytes(int64_t n, tr_dtype, tr_dtype) {
   const int64_t tiles = std::max<int64_t>(1, ceil_div(n, kTile));
-  const int64_t flags = ceil_div(tiles * 4, 256) * 256;
-  const int64_t vals = ceil_div(tiles * 8, 256) * 256;
-  return (size_t)(kWsHeader + flags + 2 * vals);
+  return (size_t)(kWsHeader + tiles * kLineBytes);
 }
 
 tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, tr_dtype yt, int64_t n, const void* carry,
                       const tr_exec* e) {
   const int64_t tiles = ceil_div(n, kTile);
   if (tiles > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "too many tiles");
-  const int64_t flags_b = ceil_div(tiles * 4, 256) * 256;
-  const int64_t vals_b = ceil_div(tiles * 8, 256) * 256;
-  const ScanWs ws{reinterpret_cast<uint32_t*>(ws_body(e)), ws_body(e) + flags_b, ws_body(e) + flags_b + vals_b};
+  const ScanWs ws{reinterpret_cast<unsigned char*>(ws_body(e))};
   const uint64_t timeout_ns = (uint64_t)(e->wait_timeout_us ? e->wait_timeout_us : 1000000u) * 1000ull;
   const int vec_ok = aligned_to(x, 16) && aligned_to(y, 16);
   cudaStream_t st = stream_of(e);
   WsHeader* hdr = ws_header(e);
   const int64_t stall = e->debug_stall_tile;
-  // every call starts from clear tile flags and status words (one memset over both) and a zero tile counter
-  tr_status s = cuda_status(cudaMemsetAsync(ws.flags, 0, (size_t)(flags_b + tiles * 8), st),
-                            "cudaMemsetAsync(scan flags)");
+  // every call starts from clear look-back lines and a zero tile counter
+  tr_status s = cuda_status(cudaMemsetAsync(ws.lines, 0, (size_t)tiles * kLineBytes, st),
+                            "cudaMemsetAsync(scan status)");
   if (!s) s = cuda_status(cudaMemsetAsync(&hdr->tile_counter, 0, sizeof(uint32_t), st), "cudaMemsetAsync(counter)");
   if (s) return s;
   auto go = [&](auto op_tag) {

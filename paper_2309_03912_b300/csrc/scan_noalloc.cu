@@ -22,10 +22,10 @@ namespace {
 
 // Largest input accepted: 2^26 elements.
 constexpr int64_t kNoAllocMaxN = int64_t(1) << 26;
-// Header + per-tile flags and two 8-byte values per tile for up to 16,384
-// tiles (tr_scan's tiles hold at least 4,096 elements, so 2^26 elements never
-// need more), 256-byte aligned as tr_scan's launcher lays them out.
-constexpr size_t kNoAllocScratchBytes = 256 + (size_t)(16384) * 4 + 2 * (size_t)(16384) * 8;
+// Header + one 128-byte look-back line per tile for up to 8,192 tiles (tr_scan's
+// tiles hold 8,192 elements, so 2^26 elements need no more); the call checks
+// the scan's own workspace size against it before launching.
+constexpr size_t kNoAllocScratchBytes = 256 + (size_t)8192 * 128;
 
 // The scratch.  In host code this name is only a stand-in for the symbol, not
 // a device address: the address is obtained with cudaGetSymbolAddress below.
@@ -82,6 +82,8 @@ extern "C" tr_status tr_scan_noalloc(const tr_map_desc* map, const void* x, tr_d
   const size_t xb = (size_t)n * dtype_size(xt), yb = (size_t)n * dtype_size(yt);
   if (n > 0 && !(xa == ya && xb == yb) && xa < ya + yb && ya < xa + xb)
     return fail(TR_ERR_INVALID_ARG, "x and y overlap partially");
+  if (scan_ws_bytes(n, xt, yt) > kNoAllocScratchBytes)
+    return fail(TR_ERR_WORKSPACE, "the fixed scratch is smaller than the scan needs for n = %lld", (long long)n);
   void* scratch = nullptr;
   if ((s = scratch_address(&scratch))) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
