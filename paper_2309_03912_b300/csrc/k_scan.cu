@@ -9,11 +9,11 @@
 //     contiguous elements per thread; threads total their rows, warps scan the
 //     totals with shuffles and the block combines warp totals;
 //   * the tile publishes its aggregate (flag A), then warp 0 looks back over
-//     32 (32-bit carries) or 128 (64-bit carries) predecessors per round,
+//     32 (128 for u64 carries) predecessors per round,
 //     summing aggregates until it meets an inclusive prefix (flag P), and
 //     publishes its own inclusive prefix.  Each tile's state has its own
-//     128-byte line; a 32-bit carry shares one 64-bit status word with its
-//     flag (one relaxed load, no fence), a 64-bit carry sits beside a flag
+//     128-byte line; u32 and FP64 carries share one 64-bit status word with
+//     their flag (one relaxed load, no fence), a u64 carry sits beside a flag
 //     released after it;
 //   * every wait is bounded by a %globaltimer deadline and an abort word: on
 //     expiry the block records TR_ERR_TIMEOUT and finishes instead of hanging.
@@ -95,18 +95,37 @@ __device__ __forceinline__ typename Op::Carry warp_sum_carry(typename Op::Carry 
 // Look-back state: one 128-byte line per tile, so that the polls of hundreds
 // of waiting tiles spread over many L2 lines instead of hammering a few (with
 // the state packed contiguously the polls contended for a handful of lines and
-// the u32 scan ran 25 % slower).  A 32-bit carry travels with its flag in one
-// 64-bit status word at the start of the line (value in the high half, flag in
-// the low bits), so one relaxed load sees both and no fence is needed; a
-// 64-bit carry sits in the same line (aggregate at byte 8, inclusive prefix at
-// byte 16) and its flag (byte 0) is released after it.
+// the u32 scan ran 25 % slower).  Where the carry and its flag fit one 64-bit
+// status word, one relaxed load sees both and no fence is needed: a u32 carry
+// takes the high half and the flag the low bits; an FP64 carry (float scans)
+// gives up its two lowest significand bits to the flag, i.e. it is published
+// truncated to 51 bits (a relative change below 2^-50, far below the FP32
+// outputs' resolution).  A u64 carry sits in the same line (aggregate at byte
+// 8, inclusive prefix at byte 16) and its flag (byte 0) is released after it.
 constexpr int kLineBytes = 128;
 struct ScanWs {
   unsigned char* lines;  // tiles x kLineBytes
 };
 
 template <class Op>
-constexpr bool kPackedStatus = sizeof(typename Op::Carry) == 4;
+constexpr bool kPackedStatus = !std::is_same<typename Op::Carry, unsigned long long>::value;
+
+template <class Op>
+__device__ __forceinline__ unsigned long long pack_status(typename Op::Carry v, uint32_t flag) {
+  if constexpr (std::is_same<typename Op::Carry, double>::value) {
+    return ((unsigned long long)__double_as_longlong(v) & ~3ull) | flag;
+  } else {
+    return ((unsigned long long)v << 32) | flag;
+  }
+}
+template <class Op>
+__device__ __forceinline__ typename Op::Carry status_value(unsigned long long w) {
+  if constexpr (std::is_same<typename Op::Carry, double>::value) {
+    return __longlong_as_double((long long)(w & ~3ull));
+  } else {
+    return (typename Op::Carry)(w >> 32);
+  }
+}
 
 __device__ __forceinline__ unsigned char* status_line(ScanWs ws, int64_t tile) {
   return ws.lines + tile * kLineBytes;
@@ -116,7 +135,7 @@ template <class Op>
 __device__ __forceinline__ void publish(ScanWs ws, int64_t tile, uint32_t flag, typename Op::Carry v) {
   unsigned char* line = status_line(ws, tile);
   if constexpr (kPackedStatus<Op>) {
-    st_relaxed_u64(reinterpret_cast<unsigned long long*>(line), ((unsigned long long)v << 32) | flag);
+    st_relaxed_u64(reinterpret_cast<unsigned long long*>(line), pack_status<Op>(v, flag));
   } else {
     *reinterpret_cast<typename Op::Carry*>(line + (flag == kFlagP ? 16 : 8)) = v;
     st_release_u32(reinterpret_cast<uint32_t*>(line), flag);
@@ -134,9 +153,9 @@ __device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typena
                                                             WsHeader* hdr, uint64_t timeout_ns, bool stall, int lane,
                                                             bool& gave_up) {
   using Carry = typename Op::Carry;
-  // predecessors read per lane and round: one for 32-bit carries, four (a
-  // 128-tile window) for 64-bit carries, whose rounds cost a fence and a
-  // second load (measured on B300: the f32 scan gains 6 %, the u32 scan none)
+  // predecessors read per lane and round: one with packed status words, four
+  // (a 128-tile window) for u64 carries, whose rounds cost a fence and a
+  // second load
   constexpr int kSlots = kPackedStatus<Op> ? 1 : 4;
   Carry excl = Carry(0);
   gave_up = false;
@@ -167,7 +186,7 @@ __device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typena
           if constexpr (kPackedStatus<Op>) {
             const unsigned long long w = ld_relaxed_u64(reinterpret_cast<const unsigned long long*>(line));
             st[m] = (uint32_t)w & 3u;
-            val[m] = (Carry)(w >> 32);
+            val[m] = status_value<Op>(w);
           } else {
             st[m] = ld_relaxed_u32(reinterpret_cast<const uint32_t*>(line)) & 3u;
           }
