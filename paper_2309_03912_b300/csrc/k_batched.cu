@@ -113,8 +113,8 @@ struct MakeBatchMap<NewtonCbrt<float, -1>> {
 
 template <class F>
 __device__ __forceinline__ Acc<float> run_item(const BatchArray& A, const BatchItem& it, int lane) {
-  const F f = MakeBatchMap<F>::make(A);
-  return warp_reduce_range<float, F>(A.x, it.start, it.start + it.count, A.aligned, f, lane, it.start + it.count);
+  const auto f = Packed<F>::make(MakeBatchMap<F>::make(A));  // coefficient pairs in registers
+  return warp_reduce_range<float>(A.x, it.start, it.start + it.count, A.aligned, f, lane, it.start + it.count);
 }
 
 __device__ __noinline__ Acc<float> dispatch_item(const BatchArray& A, const BatchItem& it, int lane) {

@@ -46,8 +46,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const In* __restrict__ x, i
       C v[kUnroll * V];
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) S::unpack(raw[u], v + u * V);
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) map_vec<V>(f, v + u * V);
+      map_vec<kUnroll * V>(f, v);
       acc.template add_vec<kUnroll * V>(v);
     } else {
       for (int u = 0; u < kUnroll; ++u) {

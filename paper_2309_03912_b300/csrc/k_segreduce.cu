@@ -293,8 +293,7 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
       float e[E];
 #pragma unroll
       for (int u = 0; u < kU; ++u) S::unpack(src[u * 32 + lane], e + u * V);  // stale past cnt: masked
-#pragma unroll
-      for (int u = 0; u < kU; ++u) map_vec<V>(f, e + u * V);  // independent chains interleave
+      map_vec<E>(f, e);  // all 16 values at once: independent chains interleave
       if (hi_s >= cb && cnt == kChunkVec) {
         acc.template add_vec<E>(e);
         return true;

@@ -43,8 +43,7 @@ __device__ __forceinline__ Acc<float> warp_reduce_range(const In* __restrict__ x
     float e[kRangeUnroll * V];
 #pragma unroll
     for (int u = 0; u < kRangeUnroll; ++u) S::unpack(raw[u], e + u * V);
-#pragma unroll
-    for (int u = 0; u < kRangeUnroll; ++u) map_vec<V>(f, e + u * V);
+    map_vec<kRangeUnroll * V>(f, e);
     acc.template add_vec<kRangeUnroll * V>(e);
   }
   for (; v < vb; v += 32) {
