@@ -234,16 +234,17 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
   if (a < n) {
     const uint4* xv = reinterpret_cast<const uint4*>(x);
     const int64_t va = a / V, vend = b / V;  // whole vectors [va, vend); elements [vend*V, b) are the tail
-    const int64_t nchunks = (vend - va + kChunkVec - 1) / kChunkVec;
-    auto issue = [&](int64_t k) {  // lane 0: fetch chunk k into its stage
+    const int nchunks = (int)((vend - va + kChunkVec - 1) / kChunkVec);
+    const int nfull = (int)((vend - va) / kChunkVec);  // chunks holding kChunkVec vectors
+    auto issue = [&](int k) {  // lane 0: fetch chunk k into its stage
       const int st = (int)(k % kStages);
-      const int64_t v0 = va + k * kChunkVec;
+      const int64_t v0 = va + (int64_t)k * kChunkVec;
       const uint32_t bytes = (uint32_t)imin<int64_t>(kChunkVec, vend - v0) * 16u;
       mbar_expect_tx(bar0 + 8 * st, bytes);
       bulk_load(ring_s + (uint32_t)st * kChunkVec * 16u, xv + v0, bytes, bar0 + 8 * st);
     };
     if (lane == 0)
-      for (int64_t k = 0; k < imin<int64_t>(kStages, nchunks); ++k) issue(k);
+      for (int k = 0; k < imin(kStages, nchunks); ++k) issue(k);
 
     const auto f = make_kernel_map<F>(P);
     const int64_t i0 = warp_lower_bound(off, nseg, a, lane);
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
     int64_t wbase = s;
     int64_t win = (wbase + lane <= nseg) ? __ldg(off + wbase + lane) : n;
     int64_t lo_s = 0, hi_s = 0;
+    int kfast = 0;  // chunks [.., kfast) are full and lie wholly inside segment s
     bool ok = true;
     auto bounds = [&]() {  // lo_s, hi_s of segment s (warp-uniform); false on invalid offsets
       if (s + 1 - wbase >= 32) {
@@ -264,6 +266,7 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
         if (lane == 0) set_status(hdr, TR_ERR_DEVICE_ASSERT, (uint32_t)s);
         return false;
       }
+      kfast = (int)imin<int64_t>(nfull, imax<int64_t>(0, hi_s - a) / (kChunkVec * V));
       return true;
     };
     ok = s < nseg && bounds();
@@ -283,21 +286,23 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
       acc = Acc<float>();
     };
     auto advance = [&]() { return ++s < nseg && bounds(); };
-    // one chunk: vectors [v0, v0 + cnt) of x, staged in ring stage st.  Every lane maps
+    // chunk k: vectors [v0, v0 + cnt) of x, staged in ring stage st.  Every lane maps
     // its kU vectors once; a chunk inside one segment is accumulated whole, any other
     // (segment boundaries inside it, or a short last chunk) by one masked pass per
     // piece of a segment, on chunk-relative element positions.
-    auto chunk = [&](int st, int64_t v0, int cnt) -> bool {
-      const int64_t ca = v0 * V, cb = (v0 + cnt) * V;
+    auto chunk = [&](int st, int k) -> bool {
       const uint4* src = ring + st * kChunkVec;
       float e[E];
 #pragma unroll
       for (int u = 0; u < kU; ++u) S::unpack(src[u * 32 + lane], e + u * V);  // stale past cnt: masked
       map_vec<E>(f, e);  // all 16 values at once: independent chains interleave
-      if (hi_s >= cb && cnt == kChunkVec) {
+      if (k < kfast) {
         acc.template add_vec<E>(e);
         return true;
       }
+      const int64_t v0 = va + (int64_t)k * kChunkVec;
+      const int cnt = (int)imin<int64_t>(kChunkVec, vend - v0);
+      const int64_t ca = v0 * V, cb = (v0 + cnt) * V;
       int lo = (int)imax<int64_t>(lo_s - ca, 0);
       while (true) {
         const int end = (int)(imin(hi_s, cb) - ca);
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
       }
     };
 
-    int64_t k = 0;
+    int k = 0;
     bool consumed = false;  // whether chunk k (where the loop stopped) was taken from the ring
     for (; k < nchunks && ok; ++k) {
       const int st = (int)(k % kStages);
@@ -322,8 +327,7 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
         consumed = false;
         break;
       }
-      const int64_t v0 = va + k * kChunkVec;
-      ok = chunk(st, v0, (int)imin<int64_t>(kChunkVec, vend - v0));
+      ok = chunk(st, k);
       if (!ok) {
         consumed = true;
         break;
@@ -388,10 +392,10 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
     // after an early stop, wait (bounded) for the copies still in flight before the shared
     // memory is released: chunks issued but not yet taken from the ring
     if (!ok) {
-      const int64_t from = consumed ? k + 1 : k;
-      const int64_t to = imin<int64_t>(nchunks, k + kStages);
-      for (int64_t j = from; j < to; ++j)
-        mbar_wait_until(bar0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), kTmaWaitNs);
+      const int from = consumed ? k + 1 : k;
+      const int to = imin(nchunks, k + kStages);
+      for (int j = from; j < to; ++j)
+        mbar_wait_until(bar0 + 8 * (j % kStages), (uint32_t)((j / kStages) & 1), kTmaWaitNs);
     }
   }
   if (lane == 0) {
