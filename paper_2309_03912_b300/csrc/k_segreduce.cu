@@ -10,8 +10,8 @@
 // per-lane sums of pairwise vector sums, then a float-float warp butterfly.
 //   * a piece that is the whole segment is written out directly;
 //   * a piece cut by the range start (head) or end (tail) goes to a per-warp
-//     workspace slot as FP64, and the last block to finish (atomic ticket
-//     after a fence) joins each cut segment's pieces in warp order in FP64.
+//     workspace slot as FP64, and a second, small kernel (one thread per
+//     warp) joins each cut segment's pieces in warp order in FP64.
 // The combination order is fixed by the grid, so results are deterministic.
 // Offsets are checked while walking (monotone, within [0, n]); a violation is
 // reported through the workspace status word instead of faulting.
@@ -65,39 +65,33 @@ __device__ __forceinline__ void write_slot(SegSlot* sl, long long seg, const Acc
   sl->through = through;
 }
 
-// Every warp has written its two slots.  The last block to arrive (ticket
-// after a fence) joins the pieces of each cut segment in warp order, in FP64.
-__device__ __forceinline__ void join_cut_segments(const RedOut& out, WsHeader* hdr, SegSlot* slots) {
-  const int64_t nw = (int64_t)gridDim.x * kWarps;
-  __shared__ bool last_block;
-  __threadfence();  // each slot writer's records are visible device-wide before the ticket
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last_block = atomicAdd(&hdr->ticket, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!last_block) return;
-  __threadfence();
-  for (int64_t w = threadIdx.x; w < nw; w += kThreads) {
-    const long long sg = __ldcg(&slots[2 * w + 1].seg);
-    if (sg < 0) continue;
-    double sum = __ldcg(&slots[2 * w + 1].sum);
-    float mn = __ldcg(&slots[2 * w + 1].mn), mx = __ldcg(&slots[2 * w + 1].mx);
-    for (int64_t w2 = w + 1; w2 < nw; ++w2) {
-      const SegSlot* h = &slots[2 * w2];
-      if (__ldcg(&h->seg) != sg) {
-        set_status(hdr, TR_ERR_DEVICE_ASSERT, (uint32_t)sg);
-        break;
-      }
-      sum += __ldcg(&h->sum);
-      mn = fminf(mn, __ldcg(&h->mn));
-      mx = fmaxf(mx, __ldcg(&h->mx));
-      if (!__ldcg(&h->through)) break;
+// Second launch: every warp of the walk has written its two slots.  One
+// thread per warp w takes w's tail piece (a segment that continues past w's
+// range) and adds the head pieces of the following warps in warp order, in
+// FP64, until the segment ends.  Threads work independently, so the slot reads
+// of all cut segments are in flight at once (a single joining block, as in the
+// usual last-block scheme, took ~20 us of serial L2 round trips at the
+// benchmark size and ~100 us with very long segments).
+__global__ void __launch_bounds__(256) k_join_cut(RedOut out, WsHeader* hdr, const SegSlot* __restrict__ slots,
+                                                  int64_t nw) {
+  const int64_t w = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (w >= nw) return;
+  const long long sg = slots[2 * w + 1].seg;
+  if (sg < 0) return;
+  double sum = slots[2 * w + 1].sum;
+  float mn = slots[2 * w + 1].mn, mx = slots[2 * w + 1].mx;
+  for (int64_t w2 = w + 1; w2 < nw; ++w2) {
+    const SegSlot* h = &slots[2 * w2];
+    if (h->seg != sg) {
+      set_status(hdr, TR_ERR_DEVICE_ASSERT, (uint32_t)sg);
+      break;
     }
-    store_result(out, sg, PartialF{sum, (double)mn, (double)mx}, true);
+    sum += h->sum;
+    mn = fminf(mn, h->mn);
+    mx = fmaxf(mx, h->mx);
+    if (!h->through) break;
   }
-  if (threadIdx.x == 0) hdr->ticket = 0;
+  store_result(out, sg, PartialF{sum, (double)mn, (double)mx}, true);
 }
 
 template <class In, class F>
@@ -155,7 +149,6 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
     if (!wrote_tail) slots[2 * gw + 1].seg = -1;
   }
 
-  join_cut_segments(out, hdr, slots);
 }
 
 
@@ -402,7 +395,6 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
     if (!wrote_head) slots[2 * gw].seg = -1;
     if (!wrote_tail) slots[2 * gw + 1].seg = -1;
   }
-  join_cut_segments(out, hdr, slots);
 }
 
 }  // namespace
@@ -443,7 +435,12 @@ tr_status launch_segreduce(const MapParams& P, const void* x, tr_dtype xt, int64
     const int64_t grid = ceil_div(warps_needed, kWarps);
     kern<<<(unsigned)grid, kThreads, smem, st>>>(static_cast<const In*>(x), n, off, n_seg, range, x_aligned, P, out,
                                                   ws_header(e), reinterpret_cast<SegSlot*>(ws_body(e)));
-    return launch_status("k_segreduce");
+    tr_status ls = launch_status("k_segreduce");
+    if (ls) return ls;
+    const int64_t nw = grid * kWarps;
+    k_join_cut<<<(unsigned)ceil_div(nw, (int64_t)256), 256, 0, st>>>(out, ws_header(e),
+                                                                    reinterpret_cast<const SegSlot*>(ws_body(e)), nw);
+    return launch_status("k_join_cut");
   });
 }
 
