@@ -534,11 +534,13 @@ def main():
         "hbm_gbs": round(achieved, 1), "frac_of_8tbs": round(achieved / NOMINAL_HBM_GBS, 4),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(achieved / hbm_peak, 4), "traffic": traffic, "peak_source": peak_src,
-                     "kernel": "k_segreduce<float, Rational<float,6,6>>", "alg_bytes_per_launch": h["alg_bytes"],
+                     "kernel": "k_segreduce_tma<float, Rational<float,6,6>> (timed with the small k_join_cut "
+                               "launch that follows it: one tr_segmented_reduce call)",
+                     "alg_bytes_per_launch": h["alg_bytes"],
                      "kernel_ms": round(kern_ms, 5), "source_sha": sha},
         "e2e": {"value": world * h["n"] / (h["e2e_ms"] * 1e-3), "unit": "elements/s",
                 "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"]},
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * args.steps,  # k_segreduce_tma + k_join_cut per step
         "clocks": h["clocks"],
         "cpu_baseline": cb,
         "configs": configs,
