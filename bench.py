@@ -214,6 +214,7 @@ def time_graph(fn, reps, stream, replays=10):
 # ----------------------------------------------------------------------------- headline
 
 def headline(args, rank, world, stream):
+    import numpy as np
     import torch
 
     from paper_2309_03912_b300 import binding as B
@@ -249,20 +250,24 @@ def headline(args, rank, world, stream):
         torch.cuda.synchronize()
         clk = Clocks(torch.cuda.current_device())
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        launches0 = B.tr_launch_count()
         with clk:
             evs[0].record(stream)
             for i in range(args.steps):
                 step()
                 evs[i + 1].record(stream)
             torch.cuda.synchronize()
+        launches = B.tr_launch_count() - launches0
         if world > 1:
             torch.distributed.barrier()
         B.tr_check(ex)
         per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
         total_ms = evs[0].elapsed_time(evs[-1])
         total_ms = max_over_ranks(total_ms, world, "cuda")
+        results = (sums.cpu().numpy(), mins.cpu().numpy(), maxs.cpu().numpy())
 
-        # end to end through the public API: pinned host input in, results out, every step
+        # end to end through the library's host-buffer entry point: every step copies x and the
+        # offsets in from page-locked host memory and the results back out, inside the timed region
         xh = torch.from_numpy(x).pin_memory()
         offh = torch.from_numpy(off).pin_memory()
         sums_h = torch.empty(nseg, dtype=torch.float64).pin_memory()
@@ -270,30 +275,35 @@ def headline(args, rank, world, stream):
         maxs_h = torch.empty(nseg, dtype=torch.float32).pin_memory()
 
         def e2e_step():
-            xd.copy_(xh, non_blocking=True)
-            offd.copy_(offh, non_blocking=True)
-            step()
-            sums_h.copy_(sums, non_blocking=True)
-            mins_h.copy_(mins, non_blocking=True)
-            maxs_h.copy_(maxs, non_blocking=True)
+            st = L.tr_segmented_reduce_host(md.ref(), xh.data_ptr(), B.TR_F32, n, offh.data_ptr(), nseg, ops,
+                                            sums_h.data_ptr(), B.TR_F64, mins_h.data_ptr(), maxs_h.data_ptr(),
+                                            xd.data_ptr(), offd.data_ptr(), sums.data_ptr(), mins.data_ptr(),
+                                            maxs.data_ptr(), exr)
+            if st:
+                raise B.TrError(st, L.tr_last_error().decode())
 
         e2e_ms, _, _ = time_launches(e2e_step, max(3, min(args.steps, 10)), 2, stream)
         B.tr_check(ex)
+        assert np.array_equal(sums_h.numpy(), results[0]), "host-buffer call differs from the device call"
     return {"n": n, "nseg": nseg, "per_ms": per, "total_ms": total_ms, "clocks": clk.summary(),
             "alg_bytes": n * 4 + (nseg + 1) * 8 + nseg * 16, "e2e_ms": e2e_ms,
-            "h2d": n * 4 + (nseg + 1) * 8, "d2h": nseg * 16}
+            "h2d": n * 4 + (nseg + 1) * 8, "d2h": nseg * 16, "launches": launches,
+            "x": x, "off": off, "map": m, "results": results}
 
 
 # ----------------------------------------------------------------------------- other workloads
 
 def other_configs(args, stream, hbm_peak):
+    """The other workloads of the path, each timed with CUDA events.  Returns
+    (records, checks): checks[name] holds the inputs and GPU outputs the CPU
+    leg compares with the oracle (outside every timed region)."""
     import numpy as np
     import torch
 
     from paper_2309_03912_b300 import binding as B
     from paper_2309_03912_b300 import inputs as I
 
-    out = {}
+    out, checks = {}, {}
     steps, warm = max(5, min(args.steps, 20)), 3
     only = [o for o in args.only.split(",") if o]
     want = lambda name: not only or name in only
@@ -319,9 +329,11 @@ def other_configs(args, stream, hbm_peak):
         f = lambda: B.tr_reduce(m, xd, 7, s[0:1], s[1:2], s[2:3], B.make_exec(ws))
         ms = time_graph(f, 20, stream)
         ms_flush = time_graph(lambda: (flush.zero_(), f()), 20, stream) - time_graph(lambda: flush.zero_(), 20, stream)
-        record("reduce_f64_horner8_2^20", ms, x.size, x.nbytes, 1,
+        name = "reduce_f64_horner8_2^20"
+        record(name, ms, x.size, x.nbytes, 1,
                {"ms_after_l2_flush": round(ms_flush, 5), "timing": "cuda graph of 20 calls",
                 "bound": "FP64 ALU (B300 FP64 is ~1/64 of FP32) and launch latency"})
+        checks[name] = {"kind": "reduce_f64", "x": x, "map": m, "got": s.cpu().numpy()}
 
     if want('mixers_2^20'):
         # u32 xorshift32: exact u64 sum + u32 -> u64 inclusive scan, N = 2^20
@@ -336,32 +348,41 @@ def other_configs(args, stream, hbm_peak):
             B.tr_reduce({"kind": "xorshift32"}, xud, 1, s64, None, None, B.make_exec(wsr))
             B.tr_scan({"kind": "xorshift32"}, xud, y64, B.make_exec(wss))
         ms = time_graph(c1b, 20, stream)
-        record("sum_u64_and_scan_u64_xorshift32_2^20", ms, xu.size, xu.nbytes * 2 + y64.numel() * 8, 2,
-               {"timing": "cuda graph of 20 calls"})
+        name = "sum_u64_and_scan_u64_xorshift32_2^20"
+        record(name, ms, xu.size, xu.nbytes * 2 + y64.numel() * 8, 2, {"timing": "cuda graph of 20 calls"})
+        checks[name] = {"kind": "mixers", "x": xu, "sum": int(s64.cpu().numpy().view(np.uint64)[0]),
+                        "scan": y64.cpu().numpy().view(np.uint64)}
         del xud, y64
 
     if want('scan_u32'):
         # u32 splitmix32 inclusive scan mod 2^32, N = 2^28
         xu = I.mixer_u32(big, stream="mixer_u32_scan")
         xud = torch.from_numpy(xu.view(np.int32)).cuda()
-        del xu
         y = torch.empty_like(xud)
         wss = B.workspace(B.tr_scan_workspace_size(xud.numel(), B.TR_U32, B.TR_U32))
         exs = B.make_exec(wss, stream=stream)
         ms, _, _ = time_launches(lambda: B.tr_scan({"kind": "splitmix32"}, xud, y, exs), steps, warm, stream)
-        record("scan_u32_splitmix32_2^28", ms, xud.numel(), xud.numel() * 8, 1)
+        B.tr_check(exs)
+        name = f"scan_u32_splitmix32_2^{args.config_log2}"
+        record(name, ms, xud.numel(), xud.numel() * 8, 1)
+        checks[name] = {"kind": "scan_u32", "x": xu, "got": y.cpu().numpy().view(np.uint32)}
         del xud, y
 
     if want('scan_f32'):
         # f32 compensated scan of x^2, N = 2^28
         xf = I.square_f32(big)
         xfd = torch.from_numpy(xf).cuda()
-        del xf
         y = torch.empty_like(xfd)
         wss = B.workspace(B.tr_scan_workspace_size(xfd.numel(), B.TR_F32, B.TR_F32))
         exs = B.make_exec(wss, stream=stream)
         ms, _, _ = time_launches(lambda: B.tr_scan(I.simple_map("square"), xfd, y, exs), steps, warm, stream)
-        record("scan_f32_square_compensated_2^28", ms, xfd.numel(), xfd.numel() * 8, 1)
+        B.tr_check(exs)
+        name = f"scan_f32_square_compensated_2^{args.config_log2}"
+        record(name, ms, xfd.numel(), xfd.numel() * 8, 1)
+        pos = np.unique(np.concatenate([np.random.default_rng(5).integers(0, xf.size, 4090),
+                                        [0, 1, 8191, 8192, xf.size - 1]]))
+        checks[name] = {"kind": "scan_f32", "x": xf, "pos": pos,
+                        "got": y[torch.from_numpy(pos).cuda()].cpu().numpy()}
         del xfd, y
 
     if want('batched'):
@@ -371,7 +392,6 @@ def other_configs(args, stream, hbm_peak):
         xs, lens, maps = I.batched(10000)
         total = int(np.sum(lens))
         dev = [torch.from_numpy(x).cuda() for x in xs]
-        del xs
         nb = len(dev)
         bs = torch.zeros(nb, dtype=torch.float64, device="cuda")
         bmn = torch.zeros(nb, dtype=torch.float32, device="cuda")
@@ -379,15 +399,18 @@ def other_configs(args, stream, hbm_peak):
         with torch.cuda.stream(stream):
             plan = B.BatchPlan(dev, maps, bs, bmn, bmx, autotune=True, stream=stream)
         ms_b, _, _ = time_launches(lambda: plan.run(stream), steps, warm, stream)
+        got = (bs.cpu().numpy(), bmn.cpu().numpy(), bmx.cpu().numpy())
         ms_eager, _, _ = time_launches(lambda: plan.run_unbatched(False, stream), 3, 1, stream)
         ms_graph, _, _ = time_launches(lambda: plan.run_unbatched(True, stream), 3, 1, stream)
         kinds = {}
         for m in maps:
             kinds[m["kind"]] = kinds.get(m["kind"], 0) + 1
-        record("batched_10000_arrays_mixed_maps", ms_b, total, total * 4, 1,
+        name = "batched_10000_arrays_mixed_maps"
+        record(name, ms_b, total, total * 4, 1,
                {"plan": plan.describe(), "arrays": nb, "maps": kinds, "unbatched_eager_ms": round(ms_eager, 4),
                 "unbatched_graph_ms": round(ms_graph, 4), "speedup_vs_eager": round(ms_eager / ms_b, 2),
                 "speedup_vs_graph": round(ms_graph / ms_b, 2), "launches_unbatched": nb})
+        checks[name] = {"kind": "batched", "xs": xs, "maps": maps, "got": got}
         plan.close()
         del dev
 
@@ -401,73 +424,208 @@ def other_configs(args, stream, hbm_peak):
         wsv = B.workspace(256)
         exv = B.make_exec(wsv, stream=stream)
         vs = max(3, steps // 4)
+        rows = np.arange(0, m, max(1, m // 512), dtype=np.int64)
+        rows_d = torch.from_numpy(rows).cuda()
         ms_tc, _, _ = time_launches(lambda: B.tr_vandermonde(xd, Cd, y, B.TR_PREC_BF16X3, exv), vs, 2, stream)
+        B.tr_check(exv)
+        got_tc = y[rows_d].cpu().numpy()
         ms_32, _, _ = time_launches(lambda: B.tr_vandermonde(xd, Cd, y, B.TR_PREC_FP32, exv), vs, 2, stream)
         B.tr_check(exv)
+        got_32 = y[rows_d].cpu().numpy()
         flops = 2.0 * m * 32 * npoly
         nbytes = m * npoly * 4 + m * 4 + C.nbytes
         vtag = f"2^{args.vander_log2_m}x32x4096"
-        record(f"vandermonde_bf16x3_{vtag}", ms_tc, m * npoly, nbytes, 1,
+        name_tc, name_32 = f"vandermonde_bf16x3_{vtag}", f"vandermonde_fp32_horner_{vtag}"
+        record(name_tc, ms_tc, m * npoly, nbytes, 1,
                {"bound": "hbm (output write)", "tflops_algorithmic": round(flops / (ms_tc * 1e-3) / 1e12, 1),
                 "tflops_tensor_executed": round(3 * flops / (ms_tc * 1e-3) / 1e12, 1),
                 "fp32_horner_ms": round(ms_32, 4), "speedup_vs_fp32_horner": round(ms_32 / ms_tc, 3)})
-        record(f"vandermonde_fp32_horner_{vtag}", ms_32, m * npoly, nbytes, 1,
+        record(name_32, ms_32, m * npoly, nbytes, 1,
                {"bound": "fp32 fma pipe / hbm", "tflops": round(flops / (ms_32 * 1e-3) / 1e12, 1)})
+        checks[name_tc] = {"kind": "vandermonde", "x": x, "C": C, "rows": rows, "got": got_tc, "bar": 1e-4}
+        checks[name_32] = {"kind": "vandermonde", "x": x, "C": C, "rows": rows, "got": got_32,
+                           "bar": 63 * 2.0 ** -24 / (1 - 63 * 2.0 ** -24)}
         del y, xd, Cd
 
     if want('f16'):
         # FP16 storage, FP32 compute: Horner deg 8 sum/min/max, N = 2^30
         xh, m = I.horner_f16(1 << 30)
         xhd = torch.from_numpy(xh).cuda()
-        del xh
         ws = B.workspace(B.tr_reduce_workspace_size(xhd.numel(), B.TR_F16))
         ex = B.make_exec(ws, stream=stream)
         s = torch.empty(1, dtype=torch.float64, device="cuda")
         mm = torch.empty(2, dtype=torch.float32, device="cuda")
         ms16, _, _ = time_launches(lambda: B.tr_reduce(m, xhd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
-        record("reduce_f16_storage_horner8_2^30", ms16, xhd.numel(), xhd.numel() * 2, 1)
+        got16 = (float(s.item()), float(mm[0].item()), float(mm[1].item()))
+        name16 = "reduce_f16_storage_horner8_2^30"
+        record(name16, ms16, xhd.numel(), xhd.numel() * 2, 1)
         # the same values in f32 storage: the plain FP32 comparison for the mixed-precision form
         xfd = xhd.float()
         del xhd
         ws = B.workspace(B.tr_reduce_workspace_size(xfd.numel(), B.TR_F32))
         ex = B.make_exec(ws, stream=stream)
         ms32, _, _ = time_launches(lambda: B.tr_reduce(m, xfd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
-        record("reduce_f32_storage_horner8_2^30", ms32, xfd.numel(), xfd.numel() * 4, 1,
-               {"f16_storage_speedup": round(ms32 / ms16, 3)})
+        got32 = (float(s.item()), float(mm[0].item()), float(mm[1].item()))
+        name32 = "reduce_f32_storage_horner8_2^30"
+        record(name32, ms32, xfd.numel(), xfd.numel() * 4, 1, {"f16_storage_speedup": round(ms32 / ms16, 3)})
+        checks[name16] = {"kind": "reduce_f32c", "x": xh, "map": m, "got": got16}
+        checks[name32] = {"kind": "reduce_f32c", "x": xh, "map": m, "got": got32, "same_values_as": name16}
         del xfd
 
     torch.cuda.synchronize()
-    return out
+    return out, checks
 
 
-# ----------------------------------------------------------------------------- CPU oracle
+# ----------------------------------------------------------------------------- CPU leg: the oracle
 
-def oracle_sample(target_elems: int = N_HEAD, repeats: int = 1):
-    """Time the oracle (as it stands, one host thread) on the first segments of
-    the headline workload holding about target_elems elements, `repeats`
-    times.  Returns (cpu_baseline record, seconds per repeat, elements)."""
+def _err(max_err, bar, checked, ok=True, **extra):
+    d = {"max_normwise": float(max_err), "bar": bar, "pass": bool(ok and max_err <= bar), "checked": checked}
+    d.update(extra)
+    return d
+
+
+def _minmax_rel(lo, hi, rlo, rhi):
+    """max |min - min_ref|, |max - max_ref| relative to max(|min_ref|, |max_ref|), non-empty results only."""
+    import numpy as np
+    lo, hi, rlo, rhi = (np.atleast_1d(np.asarray(v, dtype=np.float64)) for v in (lo, hi, rlo, rhi))
+    ne = np.isfinite(rlo)
+    if not ne.any():
+        return 0.0
+    scale = np.maximum(np.maximum(np.abs(rlo[ne]), np.abs(rhi[ne])), 1e-300)
+    return float(np.max(np.maximum(np.abs(lo[ne] - rlo[ne]), np.abs(hi[ne] - rhi[ne])) / scale))
+
+
+def _normwise(got, ref, scale):
+    import numpy as np
+    got, ref, scale = (np.atleast_1d(np.asarray(v, dtype=np.float64)) for v in (got, ref, scale))
+    e = np.abs(got - ref) / np.maximum(scale, 1e-300)
+    return float(np.max(e)) if e.size else 0.0
+
+
+def check_configs(checks, threads):
+    """The error of every result of the other workloads against the oracle
+    (host cores, outside every timed region): normwise for float sums (|s -
+    s_ref| / sum |f_ref|), relative to max |f_ref| for min / max, bit-exact
+    mismatch counts for integer results."""
+    import numpy as np
+
+    import oracle
+    errs = {}
+    for name, c in checks.items():
+        k = c["kind"]
+        if k == "reduce_f64":
+            spec = oracle.MapSpec("horner", c["map"]["cp"])
+            rs, rlo, rhi, ra = oracle.reduce_float_mt(spec, c["x"], threads)
+            s, lo, hi = c["got"]
+            exact = lo == rlo and hi == rhi
+            errs[name] = _err(abs(s - rs) / ra, 1e-13, "the sum, min and max", exact,
+                              minmax="bit-exact" if exact else "differs")
+        elif k == "mixers":
+            spec = oracle.MapSpec("xorshift32")
+            rs, _, _ = oracle.reduce_u32(spec, c["x"])
+            bad = int(np.count_nonzero(c["scan"] != oracle.scan_u32_u64(spec, c["x"]))) + int(c["sum"] != rs)
+            errs[name] = {"mismatches": bad, "bar": 0, "pass": bad == 0,
+                          "checked": f"the u64 sum and all {c['x'].size} scan outputs, bit for bit"}
+        elif k == "scan_u32":
+            bad = int(np.count_nonzero(c["got"] != oracle.scan_u32(oracle.MapSpec("splitmix32"), c["x"])))
+            errs[name] = {"mismatches": bad, "bar": 0, "pass": bad == 0,
+                          "checked": f"all {c['x'].size} outputs, bit for bit"}
+        elif k == "scan_f32":
+            ref = oracle.scan_float_sampled(oracle.MapSpec("square"), c["x"], c["pos"])
+            e = _normwise(c["got"], ref, np.abs(ref))
+            errs[name] = _err(e, 1e-5, f"{c['pos'].size} of {c['x'].size} prefixes (exact, rounded once)",
+                              metric="relative per output (all terms >= 0)")
+        elif k == "batched":
+            es, em = 0.0, 0.0
+            s, lo, hi = c["got"]
+            for a, (x, m) in enumerate(zip(c["xs"], c["maps"])):
+                spec = oracle.MapSpec(m["kind"], m.get("cp"), m.get("cq"), m.get("iters", 6))
+                rs, rlo, rhi, ra = oracle.reduce_float_mt(spec, x, threads if x.size >= 65536 else 1)
+                es = max(es, abs(s[a] - rs) / max(ra, 1e-300))
+                em = max(em, _minmax_rel(lo[a], hi[a], rlo, rhi))
+            errs[name] = _err(es, 1e-6, f"all {len(c['xs'])} arrays", em <= 1e-5,
+                              minmax_rel_max_abs=em, minmax_bar=1e-5)
+        elif k == "vandermonde":
+            y, S = oracle.vandermonde(c["x"], c["C"], c["rows"])
+            e = _normwise(c["got"], y, S)
+            errs[name] = _err(e, c["bar"], f"{c['rows'].size} of {c['x'].size} rows x {c['C'].shape[1]} polynomials",
+                              metric="|y - y_ref| / sum_k |C_kj| |x_i|^k")
+        elif k == "reduce_f32c":
+            spec = oracle.MapSpec("horner", c["map"]["cp"])
+            rs, rlo, rhi, ra = oracle.reduce_float_mt(spec, c["x"], threads)
+            s, lo, hi = c["got"]
+            em = _minmax_rel(lo, hi, rlo, rhi)
+            errs[name] = _err(abs(s - rs) / ra, 1e-6, "the whole sum, min and max", em <= 1e-5,
+                              minmax_rel_max_abs=em, minmax_bar=1e-5)
+    return errs
+
+
+def cpu_leg(h, checks, threads):
+    """The oracle on the host cores: timed on the whole headline workload with
+    one thread and with every core it may use (both runs compute the same exact
+    results), then the error of every GPU result against it."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    m = h["map"]
+    spec = oracle.MapSpec(m["kind"], m["cp"], m["cq"])
+    x, off = h["x"], h["off"]
+    t0 = time.perf_counter()
+    oracle.segmented_reduce_float_mt(spec, x, off, 1)
+    t1 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rs, rlo, rhi, ra = oracle.segmented_reduce_float_mt(spec, x, off, threads)
+    tn = time.perf_counter() - t0
+    n = x.size
+    cb = {"value": n / tn, "unit": "elements/s", "cores": threads, "kind": "oracle",
+          "sample": f"the whole headline workload ({n} elements, {off.size - 1} segments; exact sums of f and "
+                    f"|f|, min, max): {tn:.2f} s on {threads} threads, {t1:.2f} s on one",
+          "single_thread": {"value": n / t1, "unit": "elements/s", "cores": 1, "seconds": round(t1, 3)},
+          "host": {"os_cpu_count": os.cpu_count(), "affinity_cores": threads}}
+    s, lo, hi = h["results"]
+    em = _minmax_rel(lo, hi, rlo, rhi)
+    err = _err(_normwise(s, rs, ra), 1e-6, f"all {off.size - 1} segments", em <= 1e-5,
+               minmax_rel_max_abs=em, minmax_bar=1e-5, metric="|s - s_ref| / sum |f_ref| per segment")
+    t0 = time.perf_counter()
+    errs = check_configs(checks, threads) if checks else {}
+    return cb, err, errs, time.perf_counter() - t0
+
+
+def reference_arm(args):
+    """--impl reference: the oracle as it stands on the host cores, each step
+    the first segments of the headline workload holding about 2^25 elements."""
     import numpy as np
 
     import oracle
     from paper_2309_03912_b300 import inputs as I
-
+    oracle.build()
+    threads = oracle.host_threads()
     x, m, off = I.rational_segments(N_HEAD, NSEG_HEAD)
-    k = max(1, min(int(np.searchsorted(off, target_elems)), off.size - 1))
+    k = max(1, min(int(np.searchsorted(off, 1 << 25)), off.size - 1))
     sub_off = np.ascontiguousarray(off[:k + 1])
     nel = int(sub_off[-1])
     xs = np.ascontiguousarray(x[:nel])
     del x
     spec = oracle.MapSpec(m["kind"], m["cp"], m["cq"])
-    oracle.build()
+    for _ in range(args.warmup):
+        oracle.segmented_reduce_float_mt(spec, xs[:1 << 20], sub_off[sub_off <= (1 << 20)], threads)
     times = []
-    for _ in range(repeats):
+    for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.segmented_reduce_float(spec, xs, sub_off)
+        oracle.segmented_reduce_float_mt(spec, xs, sub_off, threads)
         times.append(time.perf_counter() - t0)
-    dt = statistics.mean(times)
-    return ({"value": nel / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
-             "sample": f"first {k} of {NSEG_HEAD} segments ({nel} of {N_HEAD} elements), one host thread, "
-                       f"{dt:.2f} s per pass, {repeats} pass(es)"}, times, nel)
+    value = nel / statistics.mean(times)
+    cb = {"value": value, "unit": "elements/s", "cores": threads, "kind": "oracle",
+          "sample": f"first {k} of {NSEG_HEAD} segments ({nel} of {N_HEAD} elements) per step, {threads} threads",
+          "host": {"os_cpu_count": os.cpu_count(), "affinity_cores": threads}}
+    return {"metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": N_HEAD, "n_seg": NSEG_HEAD, "step_sample_elements": nel,
+                       "parallelism": f"host, {threads} threads"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 # ----------------------------------------------------------------------------- main
@@ -479,18 +637,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        # warm-up passes on a small sample, then each step: the oracle over ~2^23 elements (~0.4 s)
-        oracle_sample(1 << 20, repeats=max(1, args.warmup))
-        cb, times, nel = oracle_sample(1 << 23, repeats=args.steps)
-        line = {"metric": METRIC, "value": cb["value"], "unit": "elements/s", "n_gpus": args.gpus,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "impl": "reference",
-                "config": {"workload": WORKLOAD, "n": N_HEAD, "n_seg": NSEG_HEAD, "step_sample_elements": nel,
-                           "parallelism": "host, one thread"},
-                "cpu_baseline": cb,
-                "e2e": {"value": cb["value"], "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        print(json.dumps(reference_arm(args)))
         return 0
 
     import torch
@@ -508,11 +655,17 @@ def main():
     stream = torch.cuda.Stream()
 
     if args.only:
-        print(json.dumps({"configs": other_configs(args, stream, hbm_peak)}))
+        recs, _ = other_configs(args, stream, hbm_peak)
+        print(json.dumps({"configs": recs}))
         return 0
     h = headline(args, rank, world, stream)
-    configs = None if (args.no_configs or rank != 0) else other_configs(args, stream, hbm_peak)
-    cb = oracle_sample()[0] if (rank == 0 and world == 1 and not args.no_cpu) else None
+    configs, checks = (None, {}) if (args.no_configs or rank != 0) else other_configs(args, stream, hbm_peak)
+    cb, err, cfg_err, check_s = None, None, {}, None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        cb, err, cfg_err, check_s = cpu_leg(h, checks, oracle.host_threads())
+        for name, e in cfg_err.items():
+            configs[name]["error"] = e
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
@@ -539,10 +692,13 @@ def main():
                      "alg_bytes_per_launch": h["alg_bytes"],
                      "kernel_ms": round(kern_ms, 5), "source_sha": sha},
         "e2e": {"value": world * h["n"] / (h["e2e_ms"] * 1e-3), "unit": "elements/s",
-                "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"]},
-        "gpu_launches": 2 * args.steps,  # k_segreduce_tma + k_join_cut per step
+                "h2d_bytes_per_step": h["h2d"], "d2h_bytes_per_step": h["d2h"],
+                "call": "tr_segmented_reduce_host (page-locked host buffers; copies enqueued by the library call)"},
+        "error": err,
+        "gpu_launches": h["launches"],
         "clocks": h["clocks"],
         "cpu_baseline": cb,
+        "oracle_check_seconds": round(check_s, 1) if check_s is not None else None,
         "configs": configs,
     }
     print(json.dumps(line))

@@ -117,6 +117,12 @@ const char* tr_status_string(tr_status s);
 /* Text describing the last failing call on this host thread ("" if none). */
 const char* tr_last_error(void);
 
+/* Number of kernels this library has enqueued in this process so far: one per
+ * kernel launch, the kernels of a graph each time the graph is launched
+ * (launches recorded during a stream capture count when recorded).  A
+ * relaxed atomic counter, for counting the kernels of a timed region. */
+uint64_t tr_launch_count(void);
+
 /* Zero-fill a workspace (cudaMemsetAsync on stream). */
 tr_status tr_workspace_init(void* d_workspace, size_t bytes, void* stream);
 
@@ -169,6 +175,21 @@ tr_status tr_segmented_reduce(const tr_map_desc* map, const void* d_x, tr_dtype 
                               const int64_t* d_offsets, int64_t n_seg, unsigned ops, void* d_sums, tr_dtype sum_t,
                               void* d_mins, void* d_maxs, const tr_exec* exec);
 
+/* tr_segmented_reduce from and to host memory, for callers whose data lives
+ * on the host: copies h_x (n elements of xt) and h_offsets (n_seg + 1 int64)
+ * into the caller's device buffers d_x and d_offsets, runs
+ * tr_segmented_reduce on them into the caller's device result buffers d_sums /
+ * d_mins / d_maxs, and copies the selected results back into h_sums / h_mins /
+ * h_maxs.  Every step is enqueued on exec->stream (cudaMemcpyAsync: page-locked
+ * host buffers make the copies asynchronous; pageable ones are staged by the
+ * driver); the host results are valid after the stream is synchronised (e.g.
+ * by tr_check).  Arguments and errors as for tr_segmented_reduce; NULL
+ * buffers for selected outputs are TR_ERR_INVALID_ARG. */
+tr_status tr_segmented_reduce_host(const tr_map_desc* map, const void* h_x, tr_dtype xt, int64_t n,
+                                   const int64_t* h_offsets, int64_t n_seg, unsigned ops, void* h_sums,
+                                   tr_dtype sum_t, void* h_mins, void* h_maxs, void* d_x, int64_t* d_offsets,
+                                   void* d_sums, void* d_mins, void* d_maxs, const tr_exec* exec);
+
 /* ---- inclusive scan ------------------------------------------------------- */
 
 tr_status tr_scan_workspace_size(int64_t n, tr_dtype xt, tr_dtype yt, size_t* bytes);
@@ -187,6 +208,29 @@ tr_status tr_scan_workspace_size(int64_t n, tr_dtype xt, tr_dtype yt, size_t* by
  * the last bit between runs (where the look-back stops depends on timing). */
 tr_status tr_scan(const tr_map_desc* map, const void* d_x, tr_dtype xt, void* d_y, tr_dtype yt, int64_t n,
                   const void* d_carry_in, const tr_exec* exec);
+
+/* ---- scan with reduction, exclusive scan ------------------------------------- */
+
+enum { TR_SCAN_INCLUSIVE = 0, TR_SCAN_EXCLUSIVE = 1 };
+
+/* tr_scan in either mode, plus, from the same single read of x, the sum, min
+ * and max of f over the whole array (ops: a mask of TR_SUM|TR_MIN|TR_MAX, 0 for
+ * none).  mode TR_SCAN_EXCLUSIVE writes y_0 = carry (or 0) and
+ * y_i = carry + f(x_0) + ... + f(x_{i-1}); TR_SCAN_INCLUSIVE is tr_scan.
+ * Results of the reduction (device memory, one element each) do not include
+ * the carry-in:
+ *   U32 -> U32:   sum_t U32 (modulo 2^32);  U32 -> U64: sum_t U64 (exact);
+ *   float scans:  sum_t F64 (the scan's FP64 total of the tiles' compensated
+ *                 sums) or F32;  min / max: F32 for float input, U32 for u32,
+ *                 ignoring NaN; for n = 0 the identities.
+ * The sum equals the last inclusive output when there is no carry-in (bit for
+ * bit for integers).  Same workspace as tr_scan; dtypes, carry, in-place and
+ * timeout rules as tr_scan.  The last tile writes the reduction; its wait for
+ * the other tiles' min / max is bounded like the look-back's
+ * (TR_ERR_TIMEOUT). */
+tr_status tr_scan_reduce(const tr_map_desc* map, const void* d_x, tr_dtype xt, void* d_y, tr_dtype yt, int64_t n,
+                         int mode, const void* d_carry_in, unsigned ops, void* d_sum, tr_dtype sum_t, void* d_min,
+                         void* d_max, const tr_exec* exec);
 
 /* ---- batched reduction ------------------------------------------------------ */
 

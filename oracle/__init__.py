@@ -67,7 +67,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-pthread",
              _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -93,6 +93,12 @@ def _load():
             lib.orc_scan_f64.argtypes = [P, P, P, I64, ctypes.c_int]
             lib.orc_scan_f64_sampled.argtypes = [P, P, I64, P, I64, P, ctypes.c_int]
             lib.orc_vandermonde.argtypes = [P, P, I32, I64, P, I64, P, P]
+            lib.orc_widen_f16.argtypes = [P, P, I64]
+            lib.orc_scan_u32_excl.argtypes = [I32, P, P, I64]
+            lib.orc_scan_u32_u64_excl.argtypes = [I32, P, P, I64]
+            lib.orc_scan_f64_excl.argtypes = [P, P, P, I64, ctypes.c_int]
+            lib.orc_reduce_mt.argtypes = [P, P, I32, I64, P, I32]
+            lib.orc_segreduce_mt.argtypes = [P, P, I32, P, I64, P, P, P, P, I32]
             _lib = lib
     return _lib
 
@@ -182,28 +188,31 @@ def mixer_range_sum(kind: str, lo: int, hi: int) -> int:
     return int(_load().orc_mixer_range_sum(KINDS[kind], lo, hi))
 
 
-def scan_u32(m: MapSpec, x) -> np.ndarray:
-    """Inclusive scan of the integer map modulo 2^32."""
+def scan_u32(m: MapSpec, x, exclusive: bool = False) -> np.ndarray:
+    """Inclusive (or exclusive) scan of the integer map modulo 2^32."""
     xu = _u32(x)
     y = np.empty_like(xu)
-    _load().orc_scan_u32(KINDS[m.kind], _ptr(xu), _ptr(y), xu.size)
+    fn = _load().orc_scan_u32_excl if exclusive else _load().orc_scan_u32
+    fn(KINDS[m.kind], _ptr(xu), _ptr(y), xu.size)
     return y
 
 
-def scan_u32_u64(m: MapSpec, x) -> np.ndarray:
-    """Inclusive scan of the integer map widened to u64 (exact)."""
+def scan_u32_u64(m: MapSpec, x, exclusive: bool = False) -> np.ndarray:
+    """Inclusive (or exclusive) scan of the integer map widened to u64 (exact)."""
     xu = _u32(x)
     y = np.empty(xu.size, np.uint64)
-    _load().orc_scan_u32_u64(KINDS[m.kind], _ptr(xu), _ptr(y), xu.size)
+    fn = _load().orc_scan_u32_u64_excl if exclusive else _load().orc_scan_u32_u64
+    fn(KINDS[m.kind], _ptr(xu), _ptr(y), xu.size)
     return y
 
 
-def scan_float(m: MapSpec, x, p: int = 24) -> np.ndarray:
-    """Inclusive scan: every prefix exact, rounded once to p bits (24: float)."""
+def scan_float(m: MapSpec, x, p: int = 24, exclusive: bool = False) -> np.ndarray:
+    """Inclusive (or exclusive) scan: every prefix exact, rounded once to p bits (24: float)."""
     xd = _f64(x)
     y = np.empty_like(xd)
     c = m._c()
-    _load().orc_scan_f64(ctypes.byref(c), _ptr(xd), _ptr(y), xd.size, int(p))
+    fn = _load().orc_scan_f64_excl if exclusive else _load().orc_scan_f64
+    fn(ctypes.byref(c), _ptr(xd), _ptr(y), xd.size, int(p))
     return y
 
 
@@ -230,3 +239,55 @@ def vandermonde(x, coef, rows=None, with_scale: bool = True):
     _load().orc_vandermonde(_ptr(xd), _ptr(cd), deg, npoly, _ptr(rr), rr.size, _ptr(y),
                             _ptr(s) if s is not None else None)
     return (y, s) if with_scale else y
+
+
+# ---------------------------------------------------------------------------- multi-threaded drivers
+
+_IN = {np.dtype(np.float64): 0, np.dtype(np.float32): 1, np.dtype(np.float16): 2}
+
+
+def host_threads() -> int:
+    """Host cores this process may run on (its CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _stored(x) -> np.ndarray:
+    """float16 / float32 / float64 arrays are passed as stored (widened exactly in C)."""
+    a = np.asarray(x)
+    if a.dtype not in _IN:
+        a = a.astype(np.float64)
+    return np.ascontiguousarray(a)
+
+
+def widen_f16(h) -> np.ndarray:
+    """Exact FP64 values of IEEE binary16 data (given as float16 or uint16 bits)."""
+    hb = np.ascontiguousarray(np.asarray(h).view(np.uint16))
+    y = np.empty(hb.size, np.float64)
+    _load().orc_widen_f16(_ptr(hb), _ptr(y), hb.size)
+    return y
+
+
+def reduce_float_mt(m: MapSpec, x, threads: int | None = None):
+    """(exact sum, min, max, exact sum of |f|) of f over x (f16 / f32 / f64
+    storage) on `threads` host threads; the same values for any thread count."""
+    xs = _stored(x)
+    out = np.empty(4, np.float64)
+    c = m._c()
+    _load().orc_reduce_mt(ctypes.byref(c), _ptr(xs), _IN[xs.dtype], xs.size, _ptr(out), int(threads or host_threads()))
+    return float(out[0]), float(out[1]), float(out[2]), float(out[3])
+
+
+def segmented_reduce_float_mt(m: MapSpec, x, offsets, threads: int | None = None):
+    """segmented_reduce_float on `threads` host threads, plus the exact sum of
+    |f| per segment: (sums, mins, maxs, abs_sums)."""
+    xs = _stored(x)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nseg = off.size - 1
+    sums, mins, maxs, abss = (np.empty(nseg, np.float64) for _ in range(4))
+    c = m._c()
+    _load().orc_segreduce_mt(ctypes.byref(c), _ptr(xs), _IN[xs.dtype], _ptr(off), nseg, _ptr(sums), _ptr(mins),
+                             _ptr(maxs), _ptr(abss), int(threads or host_threads()))
+    return sums, mins, maxs, abss

@@ -29,10 +29,16 @@
  * sequence (explicit fma in Horner, one IEEE division in P/Q), which is the
  * closest plain reading of "evaluate f in FP64".
  *
- * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no SIMD intrinsics, no
- * -ffast-math); the C library's fma() is correctly rounded (C99 7.12.13.1).
+ * The *_mt functions at the end run the same arithmetic on several host
+ * threads (to time the oracle on all cores and to check whole benchmark
+ * outputs); their results are identical to the single-thread functions.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared -pthread (no SIMD
+ * intrinsics, no -ffast-math); the C library's fma() is correctly rounded
+ * (C99 7.12.13.1).
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -290,6 +296,29 @@ void orc_scan_f64(const orc_map* m, const double* x, double* y, int64_t n, int p
   }
 }
 
+/* Exclusive scans: y_0 = 0 and y_i = f(x_0) + ... + f(x_{i-1}), each output
+ * written before its own element is added (u32 modulo 2^32; u32 widened to
+ * u64; floating point exact, rounded once to p bits). */
+void orc_scan_u32_excl(int32_t kind, const uint32_t* x, uint32_t* y, int64_t n) {
+  uint32_t s = 0;
+  for (int64_t i = 0; i < n; ++i) { y[i] = s; s += map_u32(kind, x[i]); }
+}
+
+void orc_scan_u32_u64_excl(int32_t kind, const uint32_t* x, uint64_t* y, int64_t n) {
+  uint64_t s = 0;
+  for (int64_t i = 0; i < n; ++i) { y[i] = s; s += map_u32(kind, x[i]); }
+}
+
+void orc_scan_f64_excl(const orc_map* m, const double* x, double* y, int64_t n, int p) {
+  orc_acc a;
+  acc_clear(&a);
+  int qmin = p == 24 ? ORC_BIAS - 149 : 0;
+  for (int64_t i = 0; i < n; ++i) {
+    y[i] = acc_round(&a, p, qmin);
+    acc_add(&a, map_f64(m, x[i]));
+  }
+}
+
 /* The same exact prefixes, rounded only at the sorted positions pos[0..m)
  * (for checking very long scans at sampled outputs). */
 void orc_scan_f64_sampled(const orc_map* m, const double* x, int64_t n, const int64_t* pos, int64_t npos, double* out,
@@ -328,4 +357,159 @@ void orc_vandermonde(const double* x, const double* coef, int32_t deg, int64_t n
   }
   free(c);
   free(ca);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multi-threaded drivers                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Storage types of the input array: the values are widened exactly to FP64. */
+enum { ORC_IN_F64 = 0, ORC_IN_F32 = 1, ORC_IN_F16 = 2 };
+
+/* IEEE 754 binary16 bit pattern -> its exact value: sign, 5-bit exponent
+ * (bias 15), 10-bit fraction; exponent 0 holds zeros and subnormals
+ * (fraction * 2^-24), exponent 31 infinities and NaN. */
+static double half_value(uint16_t h) {
+  int sign = h >> 15, e = (h >> 10) & 31, f = h & 1023;
+  double v;
+  if (e == 0) v = ldexp((double)f, -24);
+  else if (e == 31) v = f ? NAN : INFINITY;
+  else v = ldexp((double)(1024 + f), e - 25);
+  return sign ? -v : v;
+}
+
+void orc_widen_f16(const uint16_t* h, double* y, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) y[i] = half_value(h[i]);
+}
+
+static double load_in(const void* x, int xt, int64_t i) {
+  if (xt == ORC_IN_F32) return (double)((const float*)x)[i];
+  if (xt == ORC_IN_F16) return half_value(((const uint16_t*)x)[i]);
+  return ((const double*)x)[i];
+}
+
+/* dst += src, exactly */
+static void acc_merge(orc_acc* dst, const orc_acc* src) {
+  orc_acc t = *src;
+  acc_norm(&t);
+  for (int i = 0; i < ORC_LIMBS; ++i) dst->d[i] += t.d[i];
+  if (++dst->pending >= (1LL << 29)) acc_norm(dst);
+}
+
+/* One pass over x[lo, hi): exact sums of f and of |f|, min and max of f. */
+static void reduce_span(const orc_map* m, const void* x, int xt, int64_t lo, int64_t hi, orc_acc* sum,
+                        orc_acc* abs_sum, double* mn, double* mx) {
+  for (int64_t i = lo; i < hi; ++i) {
+    double f = map_f64(m, load_in(x, xt, i));
+    acc_add(sum, f);
+    acc_add(abs_sum, fabs(f));
+    if (f < *mn) *mn = f;
+    if (f > *mx) *mx = f;
+  }
+}
+
+typedef struct {
+  const orc_map* m;
+  const void* x;
+  int xt;
+  const int64_t* off;           /* segmented: offsets; NULL for a full reduction */
+  int64_t lo, hi;               /* element span (full) or segment span (segmented) */
+  double *sums, *mins, *maxs, *abss;
+  orc_acc sum, abs_sum;         /* full reduction: this thread's accumulators */
+  double mn, mx;
+} orc_job;
+
+static void* job_run(void* p) {
+  orc_job* j = (orc_job*)p;
+  if (!j->off) {
+    reduce_span(j->m, j->x, j->xt, j->lo, j->hi, &j->sum, &j->abs_sum, &j->mn, &j->mx);
+    return NULL;
+  }
+  orc_acc* a = (orc_acc*)malloc(2 * sizeof(orc_acc));
+  for (int64_t s = j->lo; s < j->hi; ++s) {
+    double mn = INFINITY, mx = -INFINITY;
+    acc_clear(&a[0]);
+    acc_clear(&a[1]);
+    reduce_span(j->m, j->x, j->xt, j->off[s], j->off[s + 1], &a[0], &a[1], &mn, &mx);
+    j->sums[s] = acc_round(&a[0], 53, 0);
+    j->mins[s] = mn;
+    j->maxs[s] = mx;
+    if (j->abss) j->abss[s] = acc_round(&a[1], 53, 0);
+  }
+  free(a);
+  return NULL;
+}
+
+static void run_jobs(orc_job* jobs, int nt) {
+  pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nt);
+  int* started = (int*)calloc((size_t)nt, sizeof(int));
+  for (int t = 1; t < nt; ++t) started[t] = pthread_create(&th[t], NULL, job_run, &jobs[t]) == 0;
+  job_run(&jobs[0]);
+  for (int t = 1; t < nt; ++t) {
+    if (started[t]) pthread_join(th[t], NULL);
+    else job_run(&jobs[t]);  /* no thread could be made: run it here */
+  }
+  free(started);
+  free(th);
+}
+
+/* out[0] = exact sum of f rounded to double, out[1] = min, out[2] = max,
+ * out[3] = exact sum of |f| rounded to double; x has storage type xt.  The
+ * array is cut into nthreads contiguous pieces; the pieces' exact
+ * accumulators are merged exactly, so the result does not depend on
+ * nthreads. */
+void orc_reduce_mt(const orc_map* m, const void* x, int32_t xt, int64_t n, double* out, int32_t nthreads) {
+  int nt = nthreads < 1 ? 1 : nthreads;
+  orc_job* jobs = (orc_job*)calloc((size_t)nt, sizeof(orc_job));
+  for (int t = 0; t < nt; ++t) {
+    jobs[t].m = m;
+    jobs[t].x = x;
+    jobs[t].xt = xt;
+    jobs[t].lo = n * t / nt;
+    jobs[t].hi = n * (t + 1) / nt;
+    jobs[t].mn = INFINITY;
+    jobs[t].mx = -INFINITY;
+  }
+  run_jobs(jobs, nt);
+  double mn = INFINITY, mx = -INFINITY;
+  for (int t = 1; t < nt; ++t) {
+    acc_merge(&jobs[0].sum, &jobs[t].sum);
+    acc_merge(&jobs[0].abs_sum, &jobs[t].abs_sum);
+  }
+  for (int t = 0; t < nt; ++t) {
+    if (jobs[t].mn < mn) mn = jobs[t].mn;
+    if (jobs[t].mx > mx) mx = jobs[t].mx;
+  }
+  out[0] = acc_round(&jobs[0].sum, 53, 0);
+  out[1] = mn;
+  out[2] = mx;
+  out[3] = acc_round(&jobs[0].abs_sum, 53, 0);
+  free(jobs);
+}
+
+/* orc_segreduce_f64 on nthreads threads, for input of storage type xt, plus
+ * abss[s] = exact sum of |f| over segment s rounded to double (abss may be
+ * NULL).  Thread t takes the segments starting in the t-th of nthreads equal
+ * element spans; every segment is reduced whole by one thread. */
+void orc_segreduce_mt(const orc_map* m, const void* x, int32_t xt, const int64_t* off, int64_t nseg, double* sums,
+                      double* mins, double* maxs, double* abss, int32_t nthreads) {
+  int nt = nthreads < 1 ? 1 : nthreads;
+  orc_job* jobs = (orc_job*)calloc((size_t)nt, sizeof(orc_job));
+  int64_t n = off[nseg] - off[0], s = 0;
+  for (int t = 0; t < nt; ++t) {
+    int64_t end = off[0] + n * (t + 1) / nt;
+    jobs[t].m = m;
+    jobs[t].x = x;
+    jobs[t].xt = xt;
+    jobs[t].off = off;
+    jobs[t].lo = s;
+    while (s < nseg && (t == nt - 1 || off[s] < end)) ++s;
+    jobs[t].hi = s;
+    jobs[t].sums = sums;
+    jobs[t].mins = mins;
+    jobs[t].maxs = maxs;
+    jobs[t].abss = abss;
+  }
+  run_jobs(jobs, nt);
+  free(jobs);
 }

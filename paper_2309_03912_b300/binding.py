@@ -61,6 +61,7 @@ _M = ctypes.POINTER(tr_map_desc)
 SIGNATURES = {
     "tr_status_string": ([_I32], ctypes.c_char_p),
     "tr_last_error": ([], ctypes.c_char_p),
+    "tr_launch_count": ([], ctypes.c_uint64),
     "tr_workspace_init": ([_P, _SZ, _P], _I32),
     "tr_check": ([_E], _I32),
     "tr_map": ([_M, _P, _I32, _P, _I32, _I64, _E], _I32),
@@ -68,9 +69,12 @@ SIGNATURES = {
     "tr_reduce": ([_M, _P, _I32, _I64, _U32, _P, _I32, _P, _P, _E], _I32),
     "tr_segmented_reduce_workspace_size": ([_I64, _I64, _I32, ctypes.POINTER(_SZ)], _I32),
     "tr_segmented_reduce": ([_M, _P, _I32, _I64, _P, _I64, _U32, _P, _I32, _P, _P, _E], _I32),
+    "tr_segmented_reduce_host": ([_M, _P, _I32, _I64, _P, _I64, _U32, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _E],
+                                 _I32),
     "tr_scan_workspace_size": ([_I64, _I32, _I32, ctypes.POINTER(_SZ)], _I32),
     "tr_scan": ([_M, _P, _I32, _P, _I32, _I64, _P, _E], _I32),
     "tr_scan_noalloc": ([_M, _P, _I32, _P, _I32, _I64, _P, _P, _P], _I32),
+    "tr_scan_reduce": ([_M, _P, _I32, _P, _I32, _I64, _I32, _P, _U32, _P, _I32, _P, _P, _E], _I32),
     "tr_batched_plan_create": ([_I64, _P, _P, _M, _U32, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)], _I32),
     "tr_batched_run": ([_P, _P], _I32),
     "tr_batched_run_unbatched": ([_P, _I32, _P], _I32),
@@ -167,6 +171,11 @@ def tr_scan_workspace_size(n: int, xt: int, yt: int) -> int:
 
 # ---- entry points ------------------------------------------------------------------
 
+def tr_launch_count() -> int:
+    """Kernels the library has enqueued in this process so far."""
+    return int(lib().tr_launch_count())
+
+
 def tr_workspace_init(ws: torch.Tensor, stream=None) -> None:
     s = (stream or torch.cuda.current_stream()).cuda_stream
     _check(lib().tr_workspace_init(_ptr(ws), ws.numel() * ws.element_size(), s))
@@ -202,6 +211,17 @@ def tr_scan(m: dict, x: torch.Tensor, y: torch.Tensor, ex: tr_exec, carry_in: to
     md = MapDesc(m)
     _check(lib().tr_scan(md.ref(), _ptr(x), dtype_of(x), _ptr(y), dtype_of(y), x.numel(), _ptr(carry_in),
                          ctypes.byref(ex)))
+
+
+def tr_scan_reduce(m: dict, x: torch.Tensor, y: torch.Tensor, ex: tr_exec, exclusive: bool = False,
+                   carry_in: torch.Tensor | None = None, ops: int = 0, out_sum=None, out_min=None,
+                   out_max=None) -> None:
+    """Inclusive or exclusive scan of f(x) into y, with sum / min / max of f from the same pass."""
+    md = MapDesc(m)
+    st = dtype_of(out_sum) if out_sum is not None else TR_NONE
+    _check(lib().tr_scan_reduce(md.ref(), _ptr(x), dtype_of(x), _ptr(y), dtype_of(y), x.numel(), int(exclusive),
+                                _ptr(carry_in), ops, _ptr(out_sum), st, _ptr(out_min), _ptr(out_max),
+                                ctypes.byref(ex)))
 
 
 def tr_scan_noalloc(m: dict, x: torch.Tensor, y: torch.Tensor, status: torch.Tensor | None = None,

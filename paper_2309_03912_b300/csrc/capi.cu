@@ -1,8 +1,11 @@
 // capi.cu -- the extern "C" boundary of libtr: argument validation, map
 // descriptors, workspace sizing, status reporting; dispatch to the launchers.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <set>
 #include <unordered_map>
 
 #include "internal.h"
@@ -10,6 +13,9 @@
 namespace tr {
 
 static thread_local char g_last_error[512] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 tr_status fail(tr_status s, const char* fmt, ...) {
   va_list ap;
@@ -40,16 +46,43 @@ const DevInfo& dev_info() {
   return cache.emplace(dev, d).first->second;
 }
 
+namespace {
+struct KernelKey {
+  int device;
+  const void* kernel;
+  int threads;
+  size_t bytes;
+  bool operator<(const KernelKey& o) const {
+    if (device != o.device) return device < o.device;
+    if (kernel != o.kernel) return kernel < o.kernel;
+    if (threads != o.threads) return threads < o.threads;
+    return bytes < o.bytes;
+  }
+};
+}  // namespace
+
 int blocks_per_sm(const void* kernel, int threads, size_t dyn_smem) {
   static std::mutex mu;
-  static std::unordered_map<const void*, int> cache;
+  static std::map<KernelKey, int> cache;
+  const KernelKey key{dev_info().device, kernel, threads, dyn_smem};
   std::lock_guard<std::mutex> lk(mu);
-  auto it = cache.find(kernel);
+  auto it = cache.find(key);
   if (it != cache.end()) return it->second;
   int b = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, dyn_smem) != cudaSuccess || b < 1) b = 1;
-  cache[kernel] = b;
+  cache[key] = b;
   return b;
+}
+
+tr_status ensure_dyn_smem(const void* kernel, int bytes, const char* what) {
+  static std::mutex mu;
+  static std::set<KernelKey> done;
+  const KernelKey key{dev_info().device, kernel, 0, (size_t)bytes};
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count(key)) return TR_OK;
+  tr_status s = cuda_status(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes), what);
+  if (s == TR_OK) done.insert(key);
+  return s;
 }
 
 tr_status make_tensor_map_2d(CUtensorMap* out, const void* base, CUtensorMapDataType type, uint64_t inner,
@@ -175,6 +208,8 @@ const char* tr_status_string(tr_status s) {
 
 const char* tr_last_error(void) { return g_last_error; }
 
+uint64_t tr_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 tr_status tr_workspace_init(void* ws, size_t bytes, void* stream) {
   if (!ws && bytes) return fail(TR_ERR_INVALID_ARG, "workspace is NULL");
   if (!bytes) return TR_OK;
@@ -271,6 +306,34 @@ tr_status tr_segmented_reduce(const tr_map_desc* map, const void* x, tr_dtype xt
   return launch_segreduce(P, x, xt, n, off, n_seg, ops, sums, sum_t, mins, maxs, e);
 }
 
+tr_status tr_segmented_reduce_host(const tr_map_desc* map, const void* h_x, tr_dtype xt, int64_t n,
+                                   const int64_t* h_off, int64_t n_seg, unsigned ops, void* h_sums, tr_dtype sum_t,
+                                   void* h_mins, void* h_maxs, void* d_x, int64_t* d_off, void* d_sums, void* d_mins,
+                                   void* d_maxs, const tr_exec* e) {
+  if (n < 0 || n_seg < 0) return fail(TR_ERR_INVALID_ARG, "n < 0 or n_seg < 0");
+  if (!e) return fail(TR_ERR_INVALID_ARG, "exec is NULL");
+  if ((n > 0 && (!h_x || !d_x)) || !h_off || !d_off) return fail(TR_ERR_INVALID_ARG, "input buffer is NULL");
+  const size_t xs = dtype_size(xt), ss = dtype_size(sum_t);
+  if (!xs) return fail(TR_ERR_UNSUPPORTED, "storage dtype %d", xt);
+  if ((ops & TR_SUM) && (!h_sums || !d_sums || !ss)) return fail(TR_ERR_INVALID_ARG, "sum buffers or dtype invalid");
+  if ((ops & TR_MIN) && (!h_mins || !d_mins)) return fail(TR_ERR_INVALID_ARG, "min buffers are NULL");
+  if ((ops & TR_MAX) && (!h_maxs || !d_maxs)) return fail(TR_ERR_INVALID_ARG, "max buffers are NULL");
+  cudaStream_t st = stream_of(e);
+  tr_status s = TR_OK;
+  if (n > 0) s = cuda_status(cudaMemcpyAsync(d_x, h_x, (size_t)n * xs, cudaMemcpyHostToDevice, st), "copy x");
+  if (!s) s = cuda_status(cudaMemcpyAsync(d_off, h_off, (size_t)(n_seg + 1) * 8, cudaMemcpyHostToDevice, st),
+                          "copy offsets");
+  if (!s) s = tr_segmented_reduce(map, d_x, xt, n, d_off, n_seg, ops, d_sums, sum_t, d_mins, d_maxs, e);
+  if (s) return s;
+  if (ops & TR_SUM)
+    s = cuda_status(cudaMemcpyAsync(h_sums, d_sums, (size_t)n_seg * ss, cudaMemcpyDeviceToHost, st), "copy sums");
+  if (!s && (ops & TR_MIN))
+    s = cuda_status(cudaMemcpyAsync(h_mins, d_mins, (size_t)n_seg * 4, cudaMemcpyDeviceToHost, st), "copy mins");
+  if (!s && (ops & TR_MAX))
+    s = cuda_status(cudaMemcpyAsync(h_maxs, d_maxs, (size_t)n_seg * 4, cudaMemcpyDeviceToHost, st), "copy maxs");
+  return s;
+}
+
 tr_status tr_scan_workspace_size(int64_t n, tr_dtype xt, tr_dtype yt, size_t* bytes) {
   if (!bytes || n < 0) return fail(TR_ERR_INVALID_ARG, "bad arguments");
   *bytes = scan_ws_bytes(n, xt, yt);
@@ -295,6 +358,45 @@ tr_status tr_scan(const tr_map_desc* map, const void* x, tr_dtype xt, void* y, t
   if ((s = check_exec(e, scan_ws_bytes(n, xt, yt), true))) return s;
   if (n == 0) return TR_OK;
   return launch_scan(P, x, xt, y, yt, n, carry, e);
+}
+
+tr_status tr_scan_reduce(const tr_map_desc* map, const void* x, tr_dtype xt, void* y, tr_dtype yt, int64_t n,
+                         int mode, const void* carry, unsigned ops, void* sum, tr_dtype sum_t, void* mn, void* mx,
+                         const tr_exec* e) {
+  MapParams P;
+  if (n < 0) return fail(TR_ERR_INVALID_ARG, "n < 0");
+  if (n >= (int64_t(1) << 40)) return fail(TR_ERR_INVALID_ARG, "n too large");
+  if (mode != TR_SCAN_INCLUSIVE && mode != TR_SCAN_EXCLUSIVE) return fail(TR_ERR_INVALID_ARG, "scan mode %d", mode);
+  if (ops & ~7u) return fail(TR_ERR_INVALID_ARG, "ops must be a mask of TR_SUM|TR_MIN|TR_MAX");
+  tr_status s = make_map_params(map, xt == TR_U32, &P);
+  if (s) return s;
+  const bool ok = (xt == TR_U32 && (yt == TR_U32 || yt == TR_U64)) || (is_float_storage(xt) && yt == TR_F32);
+  if (!ok) return fail(TR_ERR_UNSUPPORTED, "scan %d -> %d", xt, yt);
+  if (ops & TR_SUM) {
+    const bool st_ok = xt == TR_U32 ? sum_t == yt : (sum_t == TR_F32 || sum_t == TR_F64);
+    if (!st_ok) return fail(TR_ERR_UNSUPPORTED, "sum dtype %d for scan %d -> %d", sum_t, xt, yt);
+    if (!sum) return fail(TR_ERR_INVALID_ARG, "sum output is NULL");
+    if ((s = check_ptr(sum, sum_t, 1, "sum"))) return s;
+  }
+  const tr_dtype mt = xt == TR_U32 ? TR_U32 : TR_F32;
+  if ((ops & TR_MIN) && (!mn || (s = check_ptr(mn, mt, 1, "min")))) return s ? s : fail(TR_ERR_INVALID_ARG, "min is NULL");
+  if ((ops & TR_MAX) && (!mx || (s = check_ptr(mx, mt, 1, "max")))) return s ? s : fail(TR_ERR_INVALID_ARG, "max is NULL");
+  if ((s = check_ptr(x, xt, n, "x")) || (s = check_ptr(y, yt, n, "y"))) return s;
+  if (carry && !aligned_to(carry, dtype_size(yt))) return fail(TR_ERR_ALIGNMENT, "carry_in misaligned");
+  if (partial_overlap(x, n * dtype_size(xt), y, n * dtype_size(yt)))
+    return fail(TR_ERR_INVALID_ARG, "x and y overlap partially");
+  if (x == y && n > 0 && dtype_size(xt) != dtype_size(yt))
+    return fail(TR_ERR_INVALID_ARG, "in-place scan needs equal element sizes");
+  if ((s = check_exec(e, scan_ws_bytes(n, xt, yt), true))) return s;
+  if (n == 0 && ops == 0) return TR_OK;
+  ScanOpts o;
+  o.exclusive = mode == TR_SCAN_EXCLUSIVE;
+  o.ops = ops;
+  o.sum = sum;
+  o.sum_t = sum_t;
+  o.mn = mn;
+  o.mx = mx;
+  return launch_scan(P, x, xt, y, yt, n, carry, e, o);
 }
 
 }  // extern "C"

@@ -27,8 +27,15 @@ tr_status fail(tr_status s, const char* fmt, ...);
 // Turn a CUDA error into TR_ERR_CUDA (TR_OK for cudaSuccess).
 tr_status cuda_status(cudaError_t e, const char* what);
 
-// Check the launch of the kernel just enqueued.
-inline tr_status launch_status(const char* what) { return cuda_status(cudaGetLastError(), what); }
+// Kernel launches enqueued by the library (tr_launch_count).
+void count_launches(unsigned long long k);
+
+// Check the launch of the kernel just enqueued (and count it).
+inline tr_status launch_status(const char* what) {
+  const tr_status s = cuda_status(cudaGetLastError(), what);
+  if (s == TR_OK) count_launches(1);
+  return s;
+}
 
 size_t dtype_size(tr_dtype t);
 
@@ -38,8 +45,14 @@ inline bool aligned_to(const void* p, size_t a) { return (reinterpret_cast<uintp
 // int_input: u32 storage (mixers / identity only).
 tr_status make_map_params(const tr_map_desc* d, bool int_input, MapParams* P);
 
-// Resident blocks per SM of a kernel at a block size (cached per kernel).
+// Resident blocks per SM of a kernel at a block size and dynamic shared
+// memory size (cached per device, kernel and shape).
 int blocks_per_sm(const void* kernel, int threads, size_t dyn_smem = 0);
+
+// Allow `kernel` `bytes` of dynamic shared memory on the current device
+// (cudaFuncSetAttribute, which acts per device), once per (device, kernel,
+// bytes); thread-safe.
+tr_status ensure_dyn_smem(const void* kernel, int bytes, const char* what);
 
 inline WsHeader* ws_header(const tr_exec* e) { return static_cast<WsHeader*>(e->workspace); }
 inline char* ws_body(const tr_exec* e) { return static_cast<char*>(e->workspace) + kWsHeader; }
@@ -68,7 +81,17 @@ tr_status launch_segreduce(const MapParams& P, const void* x, tr_dtype xt, int64
                            const tr_exec* e);
 
 size_t scan_ws_bytes(int64_t n, tr_dtype xt, tr_dtype yt);
+// Options of a scan: exclusive outputs, and the sum / min / max of f taken in
+// the same pass (ops = 0: none; outputs in device memory).
+struct ScanOpts {
+  int exclusive = 0;
+  unsigned ops = 0;
+  void* sum = nullptr;
+  tr_dtype sum_t = TR_NONE;
+  void* mn = nullptr;
+  void* mx = nullptr;
+};
 tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, tr_dtype yt, int64_t n,
-                      const void* carry, const tr_exec* e);
+                      const void* carry, const tr_exec* e, const ScanOpts& opt = ScanOpts());
 
 }  // namespace tr

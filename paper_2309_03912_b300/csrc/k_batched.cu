@@ -498,7 +498,9 @@ tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, cons
 
 tr_status tr_batched_run(tr_batch_plan* p, void* stream) {
   if (!p || !p->graph) return fail(TR_ERR_INVALID_ARG, "plan is NULL");
-  return cuda_status(cudaGraphLaunch(p->graph, static_cast<cudaStream_t>(stream)), "cudaGraphLaunch");
+  const tr_status s = cuda_status(cudaGraphLaunch(p->graph, static_cast<cudaStream_t>(stream)), "cudaGraphLaunch");
+  if (s == TR_OK) count_launches(1);  // the graph holds one kernel (and a memset)
+  return s;
 }
 
 tr_status tr_batched_run_unbatched(tr_batch_plan* p, int use_graph, void* stream) {
@@ -515,7 +517,9 @@ tr_status tr_batched_run_unbatched(tr_batch_plan* p, int use_graph, void* stream
       tr_status s = capture(p, true, &p->unbatched_graph);
       if (s) return s;
     }
-    return cuda_status(cudaGraphLaunch(p->unbatched_graph, st), "cudaGraphLaunch");
+    const tr_status s = cuda_status(cudaGraphLaunch(p->unbatched_graph, st), "cudaGraphLaunch");
+    if (s == TR_OK) count_launches((unsigned long long)p->n_arrays);  // one reduce kernel per array
+    return s;
   }
   const tr_exec e{stream, p->d_reduce_ws, p->reduce_ws_bytes, 0, 0, -1};
   for (int64_t a = 0; a < p->n_arrays; ++a) {

@@ -295,6 +295,91 @@ __device__ __forceinline__ void block_totals(typename Op::T acc, typename Op::T*
   }
 }
 
+// ---- reduction in the same pass (tr_scan_reduce) ---------------------------
+// min / max travel as order-preserving unsigned keys so that one unsigned
+// maximum serves both (the minimum as the maximum of complemented keys): float
+// keys flip the sign bit of non-negative values and every bit of negative ones;
+// u32 values are their own keys.  A zero word means "no value yet" for both
+// (no non-NaN float has key 0 or complemented key 0; for u32, 0 is the identity
+// of max and ~0 that of min), so the cleared header words are the identities.
+__device__ __forceinline__ uint32_t mm_key(float v) {
+  const uint32_t b = __float_as_uint(v);
+  return b ^ ((b >> 31) ? 0xFFFFFFFFu : 0x80000000u);
+}
+__device__ __forceinline__ uint32_t mm_key(uint32_t v) { return v; }
+__device__ __forceinline__ float mm_float(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k ^ 0x80000000u) : ~k);
+}
+__device__ __forceinline__ float mm_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float mm_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ uint32_t mm_min(uint32_t a, uint32_t b) { return min(a, b); }
+__device__ __forceinline__ uint32_t mm_max(uint32_t a, uint32_t b) { return max(a, b); }
+template <class C>
+__device__ __forceinline__ C mm_lowest();
+template <>
+__device__ __forceinline__ float mm_lowest<float>() { return -INFINITY; }
+template <>
+__device__ __forceinline__ uint32_t mm_lowest<uint32_t>() { return 0u; }
+template <class C>
+__device__ __forceinline__ C mm_highest();
+template <>
+__device__ __forceinline__ float mm_highest<float>() { return INFINITY; }
+template <>
+__device__ __forceinline__ uint32_t mm_highest<uint32_t>() { return 0xFFFFFFFFu; }
+
+__device__ __forceinline__ void red_max_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The reduction outputs of a scan (ops = 0: plain scan).
+struct ScanRed {
+  void* sum;
+  void* mn;
+  void* mx;
+  int32_t sum_t;  // tr_dtype
+  uint32_t ops;
+};
+
+// Run by thread 0 of the last tile after its look-back: `total` is the sum of f
+// over all tiles (without the carry-in).  The sum is written at once; min and
+// max once every tile has folded its own in (its count is released after its
+// folds), with the wait bounded like the look-back's.
+template <class Op, class C>
+__device__ __noinline__ void finish_reduction(const ScanRed& red, WsHeader* hdr, typename Op::Carry total,
+                                              uint32_t tiles, uint64_t timeout_ns) {
+  if ((red.ops & TR_SUM) && red.sum) {
+    if constexpr (std::is_same<Op, OpF32>::value) {
+      if (red.sum_t == TR_F64)
+        *static_cast<double*>(red.sum) = total;
+      else
+        *static_cast<float*>(red.sum) = (float)total;
+    } else if constexpr (std::is_same<Op, OpU64>::value) {
+      *static_cast<unsigned long long*>(red.sum) = total;
+    } else {
+      *static_cast<uint32_t*>(red.sum) = total;
+    }
+  }
+  if (!(red.ops & (TR_MIN | TR_MAX))) return;
+  const uint64_t deadline = globaltimer_ns() + timeout_ns;
+  for (int polls = 0; ld_acquire_u32(&hdr->red_done) < tiles; ++polls) {
+    if ((polls & 15) == 15 && (globaltimer_ns() > deadline || ld_relaxed_u32(&hdr->abort) != 0u)) {
+      if (!ld_relaxed_u32(&hdr->abort)) set_status(hdr, TR_ERR_TIMEOUT, tiles);
+      return;
+    }
+  }
+  const uint32_t kmn = ld_relaxed_u32(&hdr->red_min), kmx = ld_relaxed_u32(&hdr->red_max);
+  if constexpr (std::is_same<C, float>::value) {
+    if ((red.ops & TR_MIN) && red.mn) *static_cast<float*>(red.mn) = kmn ? mm_float(~kmn) : INFINITY;
+    if ((red.ops & TR_MAX) && red.mx) *static_cast<float*>(red.mx) = kmx ? mm_float(kmx) : -INFINITY;
+  } else {
+    if ((red.ops & TR_MIN) && red.mn) *static_cast<uint32_t*>(red.mn) = ~kmn;
+    if ((red.ops & TR_MAX) && red.mx) *static_cast<uint32_t*>(red.mx) = kmx;
+  }
+}
+
 // Plain form: one tile per block, tile ids drawn in launch order.  The tile
 // moves through shared memory in both directions so that every global access
 // is a coalesced 16-byte-per-lane access: lanes load consecutive vectors, map
@@ -311,7 +396,8 @@ constexpr size_t kRowsBytes = (size_t)kThreads * kRow * 4;  // dynamic shared me
 template <class In, class F, class Op>
 __global__ void __launch_bounds__(kThreads, ScanShape<F>::blocks)
     k_scan(const In* __restrict__ x, typename Op::Out* y, int64_t n, int vec_ok, const __grid_constant__ MapParams P,
-           WsHeader* hdr, ScanWs ws, const typename Op::Out* carry_in, uint64_t timeout_ns, int64_t stall_tile) {
+           WsHeader* hdr, ScanWs ws, const typename Op::Out* carry_in, uint64_t timeout_ns, int64_t stall_tile,
+           int exclusive, ScanRed red, int64_t tiles) {
   using S = Storage<In>;
   using C = typename S::C;
   using T = typename Op::T;
@@ -325,6 +411,7 @@ __global__ void __launch_bounds__(kThreads, ScanShape<F>::blocks)
   __shared__ uint32_t s_tile;
   __shared__ T s_warp[kWarps];
   __shared__ Carry s_excl;
+  __shared__ C s_mn[kWarps], s_mx[kWarps];
   extern __shared__ __align__(16) unsigned char s_dyn[];
   C* s_rows = reinterpret_cast<C*>(s_dyn);  // kThreads * kRow values
   const int tid = threadIdx.x;
@@ -358,13 +445,51 @@ __global__ void __launch_bounds__(kThreads, ScanShape<F>::blocks)
   T acc = Op::zero();
 #pragma unroll
   for (int i = 0; i < kItems; ++i) run_add<Op>(acc, row[i]);
+  const bool minmax = (red.ops & (TR_MIN | TR_MAX)) != 0;
+  if (minmax) {  // the tile's min / max of f over its valid elements, combined per warp
+    C mn = mm_highest<C>(), mx = mm_lowest<C>();
+    const int64_t valid = full ? kItems : imax<int64_t>(0, imin<int64_t>(kItems, n - t0 - (int64_t)tid * kItems));
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      if (i < valid) {
+        mn = mm_min(mn, row[i]);
+        mx = mm_max(mx, row[i]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = mm_min(mn, __shfl_xor_sync(kFull, mn, o));
+      mx = mm_max(mx, __shfl_xor_sync(kFull, mx, o));
+    }
+    if ((tid & 31) == 0) {
+      s_mn[tid >> 5] = mn;
+      s_mx[tid >> 5] = mx;
+    }
+  }
   T warp_off, excl_lane, tile_tot;
-  block_totals<Op>(acc, s_warp, warp_off, excl_lane, tile_tot);
+  block_totals<Op>(acc, s_warp, warp_off, excl_lane, tile_tot);  // (its barrier also publishes s_mn / s_mx)
   if (tid < 32) {  // warp 0 looks back while the others wait
+    if (minmax && tid == 0) {
+      // fold the tile's min / max into the header words without waiting, then count the tile
+      // (release: the folds are visible to whoever sees the count)
+      C mn = s_mn[0], mx = s_mx[0];
+#pragma unroll
+      for (int w = 1; w < kWarps; ++w) {
+        mn = mm_min(mn, s_mn[w]);
+        mx = mm_max(mx, s_mx[w]);
+      }
+      if (mn == mn) red_max_u32(&hdr->red_min, ~mm_key(mn));  // NaN (only NaN values) adds nothing
+      if (mx == mx) red_max_u32(&hdr->red_max, mm_key(mx));
+      red_add_release_u32(&hdr->red_done, 1u);
+    }
     bool gave_up;
     const Carry e = warp_lookback<Op>(tile, Op::to_carry(tile_tot), ws, hdr, timeout_ns, tile == stall_tile, tid,
                                       gave_up);
-    if (tid == 0) s_excl = e;
+    if (tid == 0) {
+      s_excl = e;
+      if (tile == tiles - 1 && red.ops && !gave_up) finish_reduction<Op, C>(red, hdr, Op::cadd(e, Op::to_carry(tile_tot)),
+                                                                        (uint32_t)tiles, timeout_ns);
+    }
   }
   __syncthreads();
   const Carry prefix = Op::cadd(carry_in ? Carry(*carry_in) : Carry(0), s_excl);
@@ -378,10 +503,19 @@ __global__ void __launch_bounds__(kThreads, ScanShape<F>::blocks)
   }
   if constexpr (sizeof(Out) == 4) {
     Out* orow = reinterpret_cast<Out*>(row);
+    if (exclusive) {
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-      run_add<Op>(run, row[i]);
-      orow[i] = run_out<Op>(run);  // in place: this thread alone reads and writes its row
+      for (int i = 0; i < kItems; ++i) {
+        const Out o = run_out<Op>(run);
+        run_add<Op>(run, row[i]);
+        orow[i] = o;  // in place: this thread alone reads and writes its row
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) {
+        run_add<Op>(run, row[i]);
+        orow[i] = run_out<Op>(run);
+      }
     }
     __syncthreads();
     const Out* orows = reinterpret_cast<const Out*>(s_rows);
@@ -406,8 +540,13 @@ __global__ void __launch_bounds__(kThreads, ScanShape<F>::blocks)
       Out o[kPer];
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
-        run_add<Op>(run, row[g * kPer + q]);
-        o[q] = run_out<Op>(run);
+        if (exclusive) {
+          o[q] = run_out<Op>(run);
+          run_add<Op>(run, row[g * kPer + q]);
+        } else {
+          run_add<Op>(run, row[g * kPer + q]);
+          o[q] = run_out<Op>(run);
+        }
       }
       if (full) {
         st_stream(reinterpret_cast<uint4*>(y + base) + g, pack16(o));
@@ -428,8 +567,8 @@ size_t scan_ws_bytes(int64_t n, tr_dtype, tr_dtype) {
 }
 
 tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, tr_dtype yt, int64_t n, const void* carry,
-                      const tr_exec* e) {
-  const int64_t tiles = ceil_div(n, kTile);
+                      const tr_exec* e, const ScanOpts& opt) {
+  const int64_t tiles = std::max<int64_t>(1, ceil_div(n, kTile));  // n = 0 (with a reduction): one empty tile
   if (tiles > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "too many tiles");
   const ScanWs ws{reinterpret_cast<unsigned char*>(ws_body(e))};
   const uint64_t timeout_ns = (uint64_t)(e->wait_timeout_us ? e->wait_timeout_us : 1000000u) * 1000ull;
@@ -437,10 +576,13 @@ tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, t
   cudaStream_t st = stream_of(e);
   WsHeader* hdr = ws_header(e);
   const int64_t stall = e->debug_stall_tile;
-  // every call starts from clear look-back lines and a zero tile counter
-  tr_status s = cuda_status(cudaMemsetAsync(ws.lines, 0, (size_t)tiles * kLineBytes, st),
-                            "cudaMemsetAsync(scan status)");
-  if (!s) s = cuda_status(cudaMemsetAsync(&hdr->tile_counter, 0, sizeof(uint32_t), st), "cudaMemsetAsync(counter)");
+  const ScanRed red{opt.sum, opt.mn, opt.mx, (int32_t)opt.sum_t, opt.ops};
+  // every call starts from a zero tile counter, cleared reduction words and clear look-back
+  // lines: one memset from the counter through the last line (the error words before the
+  // counter are left alone)
+  unsigned char* from = reinterpret_cast<unsigned char*>(&hdr->tile_counter);
+  const size_t bytes = (size_t)(reinterpret_cast<unsigned char*>(ws.lines) - from) + (size_t)tiles * kLineBytes;
+  tr_status s = cuda_status(cudaMemsetAsync(from, 0, bytes, st), "cudaMemsetAsync(scan state)");
   if (s) return s;
   auto go = [&](auto op_tag) {
     using Op = decltype(op_tag);
@@ -449,17 +591,11 @@ tr_status launch_scan(const MapParams& P, const void* x, tr_dtype xt, void* y, t
       using F = decltype(map_tag);
       using Out = typename Op::Out;
       auto kern = k_scan<In, F, Op>;
-      static bool attr_set = false;  // per instantiation
-      if (!attr_set) {
-        tr_status a = cuda_status(
-            cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowsBytes),
-            "cudaFuncSetAttribute(k_scan)");
-        if (a) return a;
-        attr_set = true;
-      }
+      tr_status a = ensure_dyn_smem((const void*)kern, (int)kRowsBytes, "cudaFuncSetAttribute(k_scan)");
+      if (a) return a;
       kern<<<(unsigned)tiles, kThreads, kRowsBytes, st>>>(static_cast<const In*>(x), static_cast<Out*>(y), n,
                                                               vec_ok, P, hdr, ws, static_cast<const Out*>(carry),
-                                                              timeout_ns, stall);
+                                                              timeout_ns, stall, opt.exclusive, red, tiles);
       return launch_status("k_scan");
     };
   };

@@ -65,6 +65,16 @@ __device__ __forceinline__ void write_slot(SegSlot* sl, long long seg, const Acc
   sl->through = through;
 }
 
+// The two ends of the offsets contract (off[0] = 0, off[nseg] = n): the warp
+// whose range starts at element 0 and the warp whose range ends at n check
+// them; the walk itself checks every segment it visits (lo <= hi, within
+// [0, n]).  A violation is reported, never trapped.
+__device__ __forceinline__ void check_ends(const int64_t* off, int64_t nseg, int64_t n, bool first, bool last,
+                                           WsHeader* hdr) {
+  if (first && __ldg(off) != 0) set_status(hdr, TR_ERR_DEVICE_ASSERT, 0u);
+  if (last && __ldg(off + nseg) != n) set_status(hdr, TR_ERR_DEVICE_ASSERT, (uint32_t)nseg);
+}
+
 // Second launch: every warp of the walk has written its two slots.  One
 // thread per warp w takes w's tail piece (a segment that continues past w's
 // range) and adds the head pieces of the following warps in warp order, in
@@ -108,6 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
   bool wrote_head = false, wrote_tail = false;
 
   if (active) {
+    if (lane == 0) check_ends(off, nseg, n, gw == 0, last, hdr);
     const auto f = make_kernel_map<F>(P);
     const int64_t i0 = warp_lower_bound(off, nseg, a, lane);
     int64_t s = (i0 <= nseg && __ldg(off + i0) == a) ? i0 : i0 - 1;
@@ -262,7 +273,11 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
       kfast = (int)imin<int64_t>(nfull, imax<int64_t>(0, hi_s - a) / (kChunkVec * V));
       return true;
     };
+    if (lane == 0) check_ends(off, nseg, n, a == 0, last, hdr);
     ok = s < nseg && bounds();
+    // With valid offsets the first segment starts at or before a; one that starts
+    // later (off[0] > 0, reported above) must not take whole chunks before it.
+    if (lo_s > a) kfast = 0;
     bool head_open = ok && lo_s < a;
     Acc<float> acc;
     auto finish = [&]() {  // segment s ends inside this range
@@ -296,6 +311,7 @@ __global__ void __launch_bounds__(kThreads, SegShape<F>::blocks) k_segreduce_tma
       const int64_t v0 = va + (int64_t)k * kChunkVec;
       const int cnt = (int)imin<int64_t>(kChunkVec, vend - v0);
       const int64_t ca = v0 * V, cb = (v0 + cnt) * V;
+      if (lo_s >= cb) return true;  // the chunk lies before segment s (offsets breaking the contract)
       int lo = (int)imax<int64_t>(lo_s - ca, 0);
       while (true) {
         const int end = (int)(imin(hi_s, cb) - ca);
@@ -417,14 +433,8 @@ tr_status launch_segreduce(const MapParams& P, const void* x, tr_dtype xt, int64
     auto kern = tma ? k_segreduce_tma<In, F> : k_segreduce<In, F>;
     const size_t smem = tma ? (size_t)kWarps * SegShape<F>::ring : 0;
     if (tma) {
-      static bool attr_set = false;  // per instantiation
-      if (!attr_set) {
-        tr_status s = cuda_status(cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)smem),
-                                  "cudaFuncSetAttribute(k_segreduce_tma)");
-        if (s) return s;
-        attr_set = true;
-      }
+      tr_status s = ensure_dyn_smem((const void*)kern, (int)smem, "cudaFuncSetAttribute(k_segreduce_tma)");
+      if (s) return s;
     }
     const int64_t resident = (int64_t)dev_info().sm_count * blocks_per_sm((const void*)kern, kThreads, smem);
     const int64_t grid_full = std::min<int64_t>(resident, kMaxGrid);

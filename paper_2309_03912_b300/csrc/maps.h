@@ -4,12 +4,13 @@
 // host-device-compatibility tag of the paper's Sec. 4 helper; the
 // compile-time checks assert tr::hdc<F> == HDC::HstDev for the whole family.
 // The operation sequence of each map is fixed (explicit fused multiply-adds,
-// one IEEE division where a quotient appears) so that host code compiled with
-// -ffp-contract=off, device code compiled with -fmad=false and constant
-// evaluation on exactly representable inputs give identical bits.
+// one correctly rounded division where a quotient appears, div_hd) so that
+// host code compiled with -ffp-contract=off, device code compiled with
+// -fmad=false and constant evaluation on exactly representable inputs give
+// identical bits.
 //
 //   Horner     p = c_d; p = fma(p, x, c_k), k = d-1 .. 0 (ascending c)
-//   Rational   P(x) / Q(x), both by Horner
+//   Rational   P(x) / Q(x), both by Horner, one correctly rounded division
 //   NewtonCbrt y_0 = sign(x); y <- (2y + x / (y*y)) / 3, a fixed number of
 //              steps; the result is the iterate (not cbrt(x))
 //   Square     x * x
@@ -133,14 +134,14 @@ struct Rational {
     T b = q[DQ];
 #pragma unroll
     for (int k = DQ - 1; k >= 0; --k) b = fma_hd(b, x, q[k]);
-    return a / b;
+    return div_hd(a, b);
   }
   TR_HD void eval2(T x0, T x1, T& y0, T& y1) const {
     T a0, a1, b0, b1;
     horner_pair<T, DP>(p, x0, x1, a0, a1);
     horner_pair<T, DQ>(q, x0, x1, b0, b1);
-    y0 = a0 / b0;
-    y1 = a1 / b1;
+    y0 = div_hd(a0, b0);
+    y1 = div_hd(a1, b1);
   }
 };
 
@@ -150,7 +151,7 @@ struct RationalN {
   const T* p;
   const T* q;
   int dp, dq;
-  TR_HD constexpr T operator()(T x) const { return horner_eval(p, dp, x) / horner_eval(q, dq, x); }
+  TR_HD constexpr T operator()(T x) const { return div_hd(horner_eval(p, dp, x), horner_eval(q, dq, x)); }
 };
 
 // ITERS >= 0: fixed step count; ITERS < 0: run-time count in `iters`.
@@ -162,7 +163,7 @@ struct NewtonCbrt {
     T y = copysign_one(x);
     const int n = ITERS >= 0 ? ITERS : iters;
     for (int k = 0; k < n; ++k) {
-      const T s = fma_hd(T(2), y, x / (y * y));  // 2y is exact, so this is RN(2y + x/y^2)
+      const T s = fma_hd(T(2), y, div_hd(x, y * y));  // 2y is exact, so this is RN(2y + x/y^2)
       if constexpr (std::is_same<T, float>::value) {
         y = div3_hd(s);  // = RN(s / 3), division-free
       } else {

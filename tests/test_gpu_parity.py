@@ -449,3 +449,31 @@ def test_segreduce_boundaries_on_chunk_and_range_edges(orc, B, dt):
     off = np.concatenate([[0], edges, edges[::50], [n, n]]).astype(np.int64)
     off.sort()
     check_seg(orc, m, xh, off, segreduce_dev(B, m, th.cuda(), off))
+
+
+@pytest.mark.parametrize("misaligned", [False, True], ids=["tma", "unaligned"])
+@pytest.mark.parametrize("case", ["first_not_zero", "last_not_n"])
+def test_segreduce_offset_ends_reported(orc, B, misaligned, case):
+    """Offsets whose ends break the contract (off[0] = 0, off[n_seg] = n) are
+    reported as TR_ERR_DEVICE_ASSERT by tr_check on both walks (the TMA ring for
+    16-byte aligned x, plain loads otherwise), and a valid call afterwards on a
+    re-initialised workspace is exact again."""
+    n = 1_000_000
+    th, xh = host_input("f32", n, seed=31)
+    x = dev(th, 1) if misaligned else th.cuda()
+    off = np.linspace(0, n, 201).astype(np.int64)
+    bad = off.copy()
+    if case == "first_not_zero":
+        bad[0] = 5000
+    else:
+        bad[-1] = n - 100
+    m = MAPS[4]
+    ws = B.workspace(B.tr_segmented_reduce_workspace_size(n, 200, B.TR_F32))
+    sums = torch.zeros(200, dtype=torch.float64, device="cuda")
+    ex = B.make_exec(ws)
+    B.tr_segmented_reduce(m, x, torch.from_numpy(bad).cuda(), B.TR_SUM, sums, None, None, ex)
+    with pytest.raises(B.TrError) as e:
+        B.tr_check(ex)
+    assert e.value.status == 7
+    B.tr_workspace_init(ws)
+    check_seg(orc, m, xh, off, segreduce_dev(B, m, x, off))

@@ -372,3 +372,74 @@ def test_scan_sampled_matches_full_scan(orc):
     full = orc.scan_float(m, x, 24)
     pos = np.sort(g.choice(x.size, 300, replace=False))
     assert np.array_equal(orc.scan_float_sampled(m, x, pos, 24), full[pos])
+
+
+# --------------------------------------------------------------------------
+# multi-threaded drivers and binary16 widening
+# --------------------------------------------------------------------------
+
+def test_widen_f16_all_patterns(orc):
+    """Every binary16 bit pattern widens to numpy's exact float16 -> float64 value."""
+    bits = np.arange(1 << 16, dtype=np.uint16)
+    ref = bits.view(np.float16).astype(np.float64)
+    got = orc.widen_f16(bits)
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.int64), ref[~nan].view(np.int64))
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 8])
+def test_reduce_mt_equals_single_thread(orc, threads):
+    """The threaded full reduction merges exact accumulators: the same bits as
+    the single-thread oracle for any thread count, any storage type; its sum
+    of |f| equals math.fsum of |f|."""
+    g = np.random.default_rng(threads)
+    m = orc.MapSpec("rational", g.standard_normal(7), [1.0, 0.0, 0.7, 0.0, 0.2, 0.0, 0.05])
+    for dt in (np.float64, np.float32, np.float16):
+        x = g.standard_normal(100_003).astype(dt)
+        s, lo, hi, sa = orc.reduce_float_mt(m, x, threads)
+        assert (s, lo, hi) == orc.reduce_float(m, x.astype(np.float64))
+        assert sa == math.fsum(np.abs(orc.map_values(m, x.astype(np.float64))))
+    assert orc.reduce_float_mt(m, np.zeros(0), threads) == (0.0, np.inf, -np.inf, 0.0)
+
+
+@pytest.mark.parametrize("threads", [1, 2, 5, 8])
+def test_segreduce_mt_equals_single_thread(orc, threads):
+    """Threads take whole segments: the same bits as the single-thread
+    segmented oracle (empty segments included), and the per-segment sum of
+    |f| equals math.fsum of |f| over the segment."""
+    g = np.random.default_rng(10 + threads)
+    n = 50_000
+    x = g.uniform(-2, 2, n).astype(np.float32)
+    cut = np.sort(g.integers(0, n, 300))
+    off = np.concatenate([[0, 0], cut, [n, n]]).astype(np.int64)
+    m = orc.MapSpec("horner", g.standard_normal(9))
+    x64 = x.astype(np.float64)
+    sums, mins, maxs, abss = orc.segmented_reduce_float_mt(m, x, off, threads)
+    rs, rlo, rhi = orc.segmented_reduce_float(m, x64, off)
+    assert np.array_equal(sums, rs) and np.array_equal(mins, rlo) and np.array_equal(maxs, rhi)
+    f = np.abs(orc.map_values(m, x64))
+    ref_abs = [math.fsum(f[a:b]) for a, b in zip(off[:-1], off[1:])]
+    assert np.array_equal(abss, np.array(ref_abs))
+
+
+def test_exclusive_scans(orc):
+    """Exclusive scans: y_0 = 0 and y_i equals the inclusive scan at i - 1 (the
+    same exact prefix), and for f = x^2 on x = 0..n-1 the closed form
+    sum_{j<i} j^2 = (i-1) i (2i-1) / 6."""
+    g = np.random.default_rng(3)
+    x = g.integers(0, 1 << 32, 5000, dtype=np.uint64).astype(np.uint32)
+    for kind in ("xorshift32", "splitmix32"):
+        m = orc.MapSpec(kind)
+        for fn in (orc.scan_u32, orc.scan_u32_u64):
+            inc, exc = fn(m, x), fn(m, x, exclusive=True)
+            assert exc[0] == 0 and np.array_equal(exc[1:], inc[:-1])
+    n = 3000
+    i = np.arange(n, dtype=np.float64)
+    exc = orc.scan_float(orc.MapSpec("square"), i, 53, exclusive=True)
+    closed = np.array([(k - 1) * k * (2 * k - 1) // 6 for k in range(n)], dtype=np.float64)
+    assert np.array_equal(exc, closed)
+    xf = g.standard_normal(4000)
+    m = orc.MapSpec("rational", [1.0, -2.0, 0.5], [1.0, 0.0, 0.3])
+    inc, exc = orc.scan_float(m, xf, 24), orc.scan_float(m, xf, 24, exclusive=True)
+    assert exc[0] == 0.0 and np.array_equal(exc[1:], inc[:-1])
