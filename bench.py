@@ -26,6 +26,7 @@ import ctypes
 import glob
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
@@ -293,7 +294,7 @@ def headline(args, rank, world, stream):
 
 # ----------------------------------------------------------------------------- other workloads
 
-def other_configs(args, stream, hbm_peak):
+def other_configs(args, stream, hbm_peak, tensor_peak=1781.3):
     """The other workloads of the path, each timed with CUDA events.  Returns
     (records, checks): checks[name] holds the inputs and GPU outputs the CPU
     leg compares with the oracle (outside every timed region)."""
@@ -421,7 +422,7 @@ def other_configs(args, stream, hbm_peak):
         xd, Cd = torch.from_numpy(x).cuda(), torch.from_numpy(C).cuda()
         m, npoly = x.size, C.shape[1]
         y = torch.empty((m, npoly), dtype=torch.float32, device="cuda")
-        wsv = B.workspace(256)
+        wsv = B.workspace(B.tr_vandermonde_workspace_size(m, npoly))
         exv = B.make_exec(wsv, stream=stream)
         vs = max(3, steps // 4)
         rows = np.arange(0, m, max(1, m // 512), dtype=np.int64)
@@ -445,7 +446,37 @@ def other_configs(args, stream, hbm_peak):
         checks[name_tc] = {"kind": "vandermonde", "x": x, "C": C, "rows": rows, "got": got_tc, "bar": 1e-4}
         checks[name_32] = {"kind": "vandermonde", "x": x, "C": C, "rows": rows, "got": got_32,
                            "bar": 63 * 2.0 ** -24 / (1 - 63 * 2.0 ** -24)}
-        del y, xd, Cd
+        # BF16 output (half the bytes written)
+        yb = torch.empty((m, npoly), dtype=torch.bfloat16, device="cuda")
+        del y
+        ms_bf, _, _ = time_launches(lambda: B.tr_vandermonde(xd, Cd, yb, B.TR_PREC_BF16X3, exv), vs, 2, stream)
+        B.tr_check(exv)
+        name_bf = f"vandermonde_bf16x3_bf16out_{vtag}"
+        record(name_bf, ms_bf, m * npoly, m * npoly * 2 + m * 4 + C.nbytes, 1,
+               {"bound": "hbm (output write)", "tflops_algorithmic": round(flops / (ms_bf * 1e-3) / 1e12, 1)})
+        checks[name_bf] = {"kind": "vandermonde", "x": x, "C": C, "rows": rows,
+                           "got": yb[rows_d].float().cpu().numpy(), "bar": 1e-4 + 2.0 ** -8}
+        del yb
+        # the fused per-column sum / min / max without writing Y: tensor-bound
+        cs = [torch.empty(npoly, dtype=torch.float32, device="cuda") for _ in range(3)]
+        sub = 8192  # the error check: these points' column results against the oracle's full product
+        for prec, tag, nprod in ((B.TR_PREC_BF16X3, "bf16x3", 3), (B.TR_PREC_BF16X6, "bf16x6", 6)):
+            fn = lambda: B.tr_vandermonde(xd, Cd, None, prec, exv, colsum=cs[0], colmin=cs[1], colmax=cs[2])
+            ms_c, _, _ = time_launches(fn, vs, 2, stream)
+            B.tr_check(exv)
+            tf_exec = nprod * flops / (ms_c * 1e-3) / 1e12
+            name_c = f"vandermonde_{tag}_column_sum_min_max_{vtag}"
+            record(name_c, ms_c, m * npoly, m * 4 + C.nbytes + 3 * npoly * 4, 2,
+                   {"bound": "tensor", "tflops_algorithmic": round(flops / (ms_c * 1e-3) / 1e12, 1),
+                    "tflops_tensor_executed": round(tf_exec, 1), "tensor_peak_tflops_bf16": tensor_peak,
+                    "frac_of_tensor_peak": round(tf_exec / tensor_peak, 4),
+                    "note": "frac_of_measured_hbm does not apply (no Y is written)"})
+            B.tr_vandermonde(xd[:sub], Cd, None, prec, exv, colsum=cs[0], colmin=cs[1], colmax=cs[2])
+            B.tr_check(exv)
+            checks[name_c] = {"kind": "vandermonde_cols", "x": x[:sub], "C": C,
+                              "got": [c.cpu().numpy().astype(np.float64) for c in cs],
+                              "bar": 1e-4 if nprod == 3 else 1e-5}
+        del xd, Cd
 
     if want('f16'):
         # FP16 storage, FP32 compute: Horner deg 8 sum/min/max, N = 2^30
@@ -536,20 +567,39 @@ def check_configs(checks, threads):
             errs[name] = _err(e, 1e-5, f"{c['pos'].size} of {c['x'].size} prefixes (exact, rounded once)",
                               metric="relative per output (all terms >= 0)")
         elif k == "batched":
-            es, em = 0.0, 0.0
+            # the compensated sums against the exact sums of the binary32 map values (which the
+            # device reproduces bit for bit; min / max must equal theirs), and, reported beside,
+            # against FP64 evaluation of the maps (which adds the FP32 maps' own rounding)
+            es, e64, em64, mm_exact = 0.0, 0.0, 0.0, True
             s, lo, hi = c["got"]
             for a, (x, m) in enumerate(zip(c["xs"], c["maps"])):
                 spec = oracle.MapSpec(m["kind"], m.get("cp"), m.get("cq"), m.get("iters", 6))
-                rs, rlo, rhi, ra = oracle.reduce_float_mt(spec, x, threads if x.size >= 65536 else 1)
+                th = threads if x.size >= 65536 else 1
+                rs, rlo, rhi, ra = oracle.reduce_float_mt(spec, x, th, f32=True)
                 es = max(es, abs(s[a] - rs) / max(ra, 1e-300))
-                em = max(em, _minmax_rel(lo[a], hi[a], rlo, rhi))
-            errs[name] = _err(es, 1e-6, f"all {len(c['xs'])} arrays", em <= 1e-5,
-                              minmax_rel_max_abs=em, minmax_bar=1e-5)
+                mm_exact = mm_exact and lo[a] == rlo and hi[a] == rhi
+                rs, rlo, rhi, ra = oracle.reduce_float_mt(spec, x, th)
+                e64 = max(e64, abs(s[a] - rs) / max(ra, 1e-300))
+                em64 = max(em64, _minmax_rel(lo[a], hi[a], rlo, rhi))
+            errs[name] = _err(es, 1e-6, f"all {len(c['xs'])} arrays", mm_exact,
+                              metric="|s - sum f32(x)| / sum |f32(x)|, f32 = the map in binary32 (bit-identical "
+                                     "on the device)", minmax="bit-exact" if mm_exact else "differs",
+                              vs_fp64={"max_normwise": e64, "minmax_rel_max_abs": em64,
+                                       "note": "includes the FP32 evaluation error of the maps"})
         elif k == "vandermonde":
             y, S = oracle.vandermonde(c["x"], c["C"], c["rows"])
             e = _normwise(c["got"], y, S)
             errs[name] = _err(e, c["bar"], f"{c['rows'].size} of {c['x'].size} rows x {c['C'].shape[1]} polynomials",
                               metric="|y - y_ref| / sum_k |C_kj| |x_i|^k")
+        elif k == "vandermonde_cols":
+            y, S = oracle.vandermonde(c["x"], c["C"])
+            s, lo, hi = c["got"]
+            rs = np.array([math.fsum(y[:, j]) for j in range(y.shape[1])])
+            es = _normwise(s, rs, S.sum(axis=0))
+            em = max(_normwise(lo, y.min(axis=0), S.max(axis=0)), _normwise(hi, y.max(axis=0), S.max(axis=0)))
+            errs[name] = _err(max(es, em), c["bar"], f"the column sum, min and max over the first {c['x'].size} "
+                              f"points, all {y.shape[1]} polynomials (a run on those points)",
+                              metric="sums: / sum_i S_ij; min, max: / max_i S_ij", sum_err=es, minmax_err=em)
         elif k == "reduce_f32c":
             spec = oracle.MapSpec("horner", c["map"]["cp"])
             rs, rlo, rhi, ra = oracle.reduce_float_mt(spec, c["x"], threads)
@@ -585,8 +635,13 @@ def cpu_leg(h, checks, threads):
           "host": {"os_cpu_count": os.cpu_count(), "affinity_cores": threads}}
     s, lo, hi = h["results"]
     em = _minmax_rel(lo, hi, rlo, rhi)
+    r32 = oracle.segmented_reduce_float_mt(spec, x, off, threads, f32=True)
+    ne = np.isfinite(r32[1])
     err = _err(_normwise(s, rs, ra), 1e-6, f"all {off.size - 1} segments", em <= 1e-5,
-               minmax_rel_max_abs=em, minmax_bar=1e-5, metric="|s - s_ref| / sum |f_ref| per segment")
+               minmax_rel_max_abs=em, minmax_bar=1e-5, metric="|s - s_ref| / sum |f_ref| per segment (FP64 f)",
+               vs_binary32_values={"max_normwise": _normwise(s, r32[0], r32[3]),
+                                   "minmax": "bit-exact" if (np.array_equal(lo[ne], r32[1][ne]) and
+                                                             np.array_equal(hi[ne], r32[2][ne])) else "differs"})
     t0 = time.perf_counter()
     errs = check_configs(checks, threads) if checks else {}
     return cb, err, errs, time.perf_counter() - t0
@@ -651,15 +706,15 @@ def main():
     if not os.path.exists(B.LIB_PATH):
         Bd.build()
     B.lib()
-    hbm_peak, _, peak_src = peaks()
+    hbm_peak, tensor_peak, peak_src = peaks()
     stream = torch.cuda.Stream()
 
     if args.only:
-        recs, _ = other_configs(args, stream, hbm_peak)
+        recs, _ = other_configs(args, stream, hbm_peak, tensor_peak)
         print(json.dumps({"configs": recs}))
         return 0
     h = headline(args, rank, world, stream)
-    configs, checks = (None, {}) if (args.no_configs or rank != 0) else other_configs(args, stream, hbm_peak)
+    configs, checks = (None, {}) if (args.no_configs or rank != 0) else other_configs(args, stream, hbm_peak, tensor_peak)
     cb, err, cfg_err, check_s = None, None, {}, None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle

@@ -271,26 +271,43 @@ tr_status tr_batched_plan_destroy(tr_batch_plan* plan);
 
 /* ---- dense Vandermonde product ---------------------------------------------- */
 
-enum { TR_PREC_BF16X3 = 0, TR_PREC_FP32 = 1 };
+enum { TR_PREC_BF16X3 = 0, TR_PREC_FP32 = 1, TR_PREC_BF16X6 = 2 };
 
-/* Workspace of tr_vandermonde (a status header; 256 bytes). */
-tr_status tr_vandermonde_workspace_size(size_t* bytes);
+/* Workspace of tr_vandermonde for npoly polynomials: a status header and the
+ * per-column partial results of the tensor path. */
+tr_status tr_vandermonde_workspace_size(int64_t m, int64_t npoly, size_t* bytes);
 
-/* Many polynomials at many points: Y = V(x) C, Y[i][j] = sum_k C[k][j] x_i^k.
+/* Many polynomials at many points (the dense workload of the brief: 4096
+ * polynomials of degree 31 at 2^20 points, "Vandermonde GEMM on tcgen05/TMEM"
+ * with split-BF16): Y = V(x) C, Y[i][j] = sum_k C[k][j] x_i^k, written out
+ * and/or reduced per column (polynomial j) over the points.
  *   d_x     m FP32 points;  d_coef (deg+1) x npoly FP32, row-major, row k
  *           holding the power-k coefficients of all polynomials (deg <= 31);
- *   d_y     m x npoly FP32, row-major.
- * TR_PREC_BF16X3: split-BF16 on the tcgen05 tensor cores (Henry, Tang &
- *   Heinecke, ARITH 2019): V = Vh + Vl, C = Ch + Cl, Y ~= Vh Ch + Vh Cl + Vl Ch
- *   accumulated in FP32 in tensor memory; V is generated on the fly from x.
- *   Needs m % 128 == 0, npoly % 256 == 0, a 16-byte aligned d_y and a
- *   workspace of tr_vandermonde_workspace_size() bytes (its status word
- *   reports a device-side timeout through tr_check).  Error, normwise against
- *   S[i][j] = sum_k |C[k][j]| |x_i|^k: about 1e-5.
- * TR_PREC_FP32: FP32 Horner with fma on the CUDA cores, any m and npoly.
- * Rows beyond deg are treated as zero coefficients. */
+ *   d_y     m x npoly row-major in yt: TR_F32, TR_BF16 (rounded to nearest
+ *           even from the FP32 result) or TR_NONE (not written; d_y ignored);
+ *   d_colsum / d_colmin / d_colmax (each nullable, npoly FP32, device): sum,
+ *           minimum and maximum of column j over the m points, taken from the
+ *           FP32 results in the same pass (partials combined in FP64 in a
+ *           fixed order: deterministic).
+ * precision
+ *   TR_PREC_BF16X3 / TR_PREC_BF16X6: split-BF16 on the tcgen05 tensor cores
+ *     (Henry, Tang & Heinecke, ARITH 2019): powers and coefficients are split
+ *     into 2 (x3: V1C1 + V1C2 + V2C1) or 3 (x6: all products of parts whose
+ *     orders sum to at most 2) bf16 parts, accumulated in FP32 in tensor
+ *     memory; V is generated on the fly from x.  Error, normwise against
+ *     S[i][j] = sum_k |C[k][j]| |x_i|^k: about 2e-5 (x3), 1e-6 (x6).  Any m;
+ *     FP32 output needs npoly % 4 == 0, BF16 output npoly % 8 == 0, and a
+ *     16-byte aligned d_y; TR_NONE output any npoly.  Needs a workspace of
+ *     tr_vandermonde_workspace_size() bytes (its status word reports a
+ *     device-side timeout through tr_check).  Two launches when a column
+ *     result is requested, one otherwise.
+ *   TR_PREC_FP32: FP32 Horner with fma on the CUDA cores (the comparison);
+ *     FP32 output only, no column results, any m and npoly, no workspace.
+ * Rows of C beyond deg are treated as zero.  Nothing requested (TR_NONE and
+ * no column output) is TR_ERR_INVALID_ARG. */
 tr_status tr_vandermonde(const float* d_x, int64_t m, const float* d_coef, int32_t deg, int64_t npoly,
-                         int precision, float* d_y, const tr_exec* exec);
+                         int precision, void* d_y, tr_dtype yt, float* d_colsum, float* d_colmin, float* d_colmax,
+                         const tr_exec* exec);
 
 /* ---- inclusive scan without a workspace -------------------------------------- */
 

@@ -97,8 +97,9 @@ def _load():
             lib.orc_scan_u32_excl.argtypes = [I32, P, P, I64]
             lib.orc_scan_u32_u64_excl.argtypes = [I32, P, P, I64]
             lib.orc_scan_f64_excl.argtypes = [P, P, P, I64, ctypes.c_int]
-            lib.orc_reduce_mt.argtypes = [P, P, I32, I64, P, I32]
-            lib.orc_segreduce_mt.argtypes = [P, P, I32, P, I64, P, P, P, P, I32]
+            lib.orc_reduce_mt.argtypes = [P, I32, P, I32, I64, P, I32]
+            lib.orc_segreduce_mt.argtypes = [P, I32, P, I32, P, I64, P, P, P, P, I32]
+            lib.orc_map_f32.argtypes = [P, P, P, I64]
             _lib = lib
     return _lib
 
@@ -270,24 +271,37 @@ def widen_f16(h) -> np.ndarray:
     return y
 
 
-def reduce_float_mt(m: MapSpec, x, threads: int | None = None):
+def map_values_f32(m: MapSpec, x) -> np.ndarray:
+    """y_i = f(x_i) evaluated in IEEE binary32 (the map's own operation sequence,
+    one binary32 rounding per operation), widened to FP64.  Inputs and
+    coefficients must be binary32 values."""
+    xd = _f64(x)
+    y = np.empty_like(xd)
+    c = m._c()
+    _load().orc_map_f32(ctypes.byref(c), _ptr(xd), _ptr(y), xd.size)
+    return y
+
+
+def reduce_float_mt(m: MapSpec, x, threads: int | None = None, f32: bool = False):
     """(exact sum, min, max, exact sum of |f|) of f over x (f16 / f32 / f64
-    storage) on `threads` host threads; the same values for any thread count."""
+    storage) on `threads` host threads; the same values for any thread count.
+    f32: f evaluated in binary32 (map_values_f32) instead of FP64."""
     xs = _stored(x)
     out = np.empty(4, np.float64)
     c = m._c()
-    _load().orc_reduce_mt(ctypes.byref(c), _ptr(xs), _IN[xs.dtype], xs.size, _ptr(out), int(threads or host_threads()))
+    _load().orc_reduce_mt(ctypes.byref(c), int(f32), _ptr(xs), _IN[xs.dtype], xs.size, _ptr(out),
+                          int(threads or host_threads()))
     return float(out[0]), float(out[1]), float(out[2]), float(out[3])
 
 
-def segmented_reduce_float_mt(m: MapSpec, x, offsets, threads: int | None = None):
+def segmented_reduce_float_mt(m: MapSpec, x, offsets, threads: int | None = None, f32: bool = False):
     """segmented_reduce_float on `threads` host threads, plus the exact sum of
-    |f| per segment: (sums, mins, maxs, abs_sums)."""
+    |f| per segment: (sums, mins, maxs, abs_sums); f32 as for reduce_float_mt."""
     xs = _stored(x)
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     nseg = off.size - 1
     sums, mins, maxs, abss = (np.empty(nseg, np.float64) for _ in range(4))
     c = m._c()
-    _load().orc_segreduce_mt(ctypes.byref(c), _ptr(xs), _IN[xs.dtype], _ptr(off), nseg, _ptr(sums), _ptr(mins),
-                             _ptr(maxs), _ptr(abss), int(threads or host_threads()))
+    _load().orc_segreduce_mt(ctypes.byref(c), int(f32), _ptr(xs), _IN[xs.dtype], _ptr(off), nseg, _ptr(sums),
+                             _ptr(mins), _ptr(maxs), _ptr(abss), int(threads or host_threads()))
     return sums, mins, maxs, abss

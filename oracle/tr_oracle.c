@@ -203,6 +203,37 @@ static uint32_t map_u32(int kind, uint32_t x) {
   }
 }
 
+/* The same maps evaluated in IEEE binary32 (the precision of the FP32-compute
+ * paths): coefficients and inputs are binary32 values (the callers pass doubles
+ * that are exactly representable), every operation is one binary32 operation
+ * of the stated sequence -- fmaf in Horner, one float division in P/Q, the
+ * Newton step RN(RN(2y + RN(x / RN(y*y))) / 3) with 2y exact -- and the result
+ * is returned widened exactly to double. */
+static float horner_f32(const double* c, int d, float x) {
+  float p = (float)c[d];
+  for (int k = d - 1; k >= 0; --k) p = fmaf(p, x, (float)c[k]);
+  return p;
+}
+
+static float map_f32(const orc_map* m, float x) {
+  switch (m->kind) {
+    case ORC_IDENTITY: return x;
+    case ORC_SQUARE: return x * x;
+    case ORC_HORNER: return horner_f32(m->cp, m->deg_p, x);
+    case ORC_RATIONAL: return horner_f32(m->cp, m->deg_p, x) / horner_f32(m->cq, m->deg_q, x);
+    case ORC_NEWTON_CBRT: {
+      float y = copysignf(1.0f, x);
+      for (int k = 0; k < m->iters; ++k) y = fmaf(2.0f, y, x / (y * y)) / 3.0f;
+      return y;
+    }
+    default: return NAN;
+  }
+}
+
+void orc_map_f32(const orc_map* m, const double* x, double* y, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) y[i] = (double)map_f32(m, (float)x[i]);
+}
+
 void orc_map_f64(const orc_map* m, const double* x, double* y, int64_t n) {
   for (int64_t i = 0; i < n; ++i) y[i] = map_f64(m, x[i]);
 }
@@ -396,11 +427,13 @@ static void acc_merge(orc_acc* dst, const orc_acc* src) {
   if (++dst->pending >= (1LL << 29)) acc_norm(dst);
 }
 
-/* One pass over x[lo, hi): exact sums of f and of |f|, min and max of f. */
-static void reduce_span(const orc_map* m, const void* x, int xt, int64_t lo, int64_t hi, orc_acc* sum,
+/* One pass over x[lo, hi): exact sums of f and of |f|, min and max of f, with
+ * f evaluated in FP64 (f32 = 0) or in binary32 (f32 = 1). */
+static void reduce_span(const orc_map* m, int f32, const void* x, int xt, int64_t lo, int64_t hi, orc_acc* sum,
                         orc_acc* abs_sum, double* mn, double* mx) {
   for (int64_t i = lo; i < hi; ++i) {
-    double f = map_f64(m, load_in(x, xt, i));
+    double v = load_in(x, xt, i);
+    double f = f32 ? (double)map_f32(m, (float)v) : map_f64(m, v);
     acc_add(sum, f);
     acc_add(abs_sum, fabs(f));
     if (f < *mn) *mn = f;
@@ -410,6 +443,7 @@ static void reduce_span(const orc_map* m, const void* x, int xt, int64_t lo, int
 
 typedef struct {
   const orc_map* m;
+  int f32;                      /* evaluate f in binary32 */
   const void* x;
   int xt;
   const int64_t* off;           /* segmented: offsets; NULL for a full reduction */
@@ -422,7 +456,7 @@ typedef struct {
 static void* job_run(void* p) {
   orc_job* j = (orc_job*)p;
   if (!j->off) {
-    reduce_span(j->m, j->x, j->xt, j->lo, j->hi, &j->sum, &j->abs_sum, &j->mn, &j->mx);
+    reduce_span(j->m, j->f32, j->x, j->xt, j->lo, j->hi, &j->sum, &j->abs_sum, &j->mn, &j->mx);
     return NULL;
   }
   orc_acc* a = (orc_acc*)malloc(2 * sizeof(orc_acc));
@@ -430,7 +464,7 @@ static void* job_run(void* p) {
     double mn = INFINITY, mx = -INFINITY;
     acc_clear(&a[0]);
     acc_clear(&a[1]);
-    reduce_span(j->m, j->x, j->xt, j->off[s], j->off[s + 1], &a[0], &a[1], &mn, &mx);
+    reduce_span(j->m, j->f32, j->x, j->xt, j->off[s], j->off[s + 1], &a[0], &a[1], &mn, &mx);
     j->sums[s] = acc_round(&a[0], 53, 0);
     j->mins[s] = mn;
     j->maxs[s] = mx;
@@ -454,15 +488,18 @@ static void run_jobs(orc_job* jobs, int nt) {
 }
 
 /* out[0] = exact sum of f rounded to double, out[1] = min, out[2] = max,
- * out[3] = exact sum of |f| rounded to double; x has storage type xt.  The
+ * out[3] = exact sum of |f| rounded to double; x has storage type xt; f in
+ * FP64, or in binary32 when f32 != 0.  The
  * array is cut into nthreads contiguous pieces; the pieces' exact
  * accumulators are merged exactly, so the result does not depend on
  * nthreads. */
-void orc_reduce_mt(const orc_map* m, const void* x, int32_t xt, int64_t n, double* out, int32_t nthreads) {
+void orc_reduce_mt(const orc_map* m, int32_t f32, const void* x, int32_t xt, int64_t n, double* out,
+                   int32_t nthreads) {
   int nt = nthreads < 1 ? 1 : nthreads;
   orc_job* jobs = (orc_job*)calloc((size_t)nt, sizeof(orc_job));
   for (int t = 0; t < nt; ++t) {
     jobs[t].m = m;
+    jobs[t].f32 = f32;
     jobs[t].x = x;
     jobs[t].xt = xt;
     jobs[t].lo = n * t / nt;
@@ -491,14 +528,15 @@ void orc_reduce_mt(const orc_map* m, const void* x, int32_t xt, int64_t n, doubl
  * abss[s] = exact sum of |f| over segment s rounded to double (abss may be
  * NULL).  Thread t takes the segments starting in the t-th of nthreads equal
  * element spans; every segment is reduced whole by one thread. */
-void orc_segreduce_mt(const orc_map* m, const void* x, int32_t xt, const int64_t* off, int64_t nseg, double* sums,
-                      double* mins, double* maxs, double* abss, int32_t nthreads) {
+void orc_segreduce_mt(const orc_map* m, int32_t f32, const void* x, int32_t xt, const int64_t* off, int64_t nseg,
+                      double* sums, double* mins, double* maxs, double* abss, int32_t nthreads) {
   int nt = nthreads < 1 ? 1 : nthreads;
   orc_job* jobs = (orc_job*)calloc((size_t)nt, sizeof(orc_job));
   int64_t n = off[nseg] - off[0], s = 0;
   for (int t = 0; t < nt; ++t) {
     int64_t end = off[0] + n * (t + 1) / nt;
     jobs[t].m = m;
+    jobs[t].f32 = f32;
     jobs[t].x = x;
     jobs[t].xt = xt;
     jobs[t].off = off;

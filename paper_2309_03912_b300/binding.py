@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_PKG, "libtr.so")
 
 TR_F16, TR_BF16, TR_F32, TR_F64, TR_U32, TR_U64, TR_NONE = 0, 1, 2, 3, 4, 5, 15
 TR_SUM, TR_MIN, TR_MAX = 1, 2, 4
-TR_PREC_BF16X3, TR_PREC_FP32 = 0, 1
+TR_PREC_BF16X3, TR_PREC_FP32, TR_PREC_BF16X6 = 0, 1, 2
 MAP_KINDS = {"identity": 0, "square": 1, "horner": 2, "rational": 3, "newton_cbrt": 4,
              "xorshift32": 5, "splitmix32": 6}
 STATUS = {0: "TR_OK", 1: "TR_ERR_INVALID_ARG", 2: "TR_ERR_ALIGNMENT", 3: "TR_ERR_UNSUPPORTED",
@@ -80,8 +80,8 @@ SIGNATURES = {
     "tr_batched_run_unbatched": ([_P, _I32, _P], _I32),
     "tr_batched_plan_describe": ([_P], ctypes.c_char_p),
     "tr_batched_plan_destroy": ([_P], _I32),
-    "tr_vandermonde_workspace_size": ([ctypes.POINTER(_SZ)], _I32),
-    "tr_vandermonde": ([_P, _I64, _P, _I32, _I64, _I32, _P, _E], _I32),
+    "tr_vandermonde_workspace_size": ([_I64, _I64, ctypes.POINTER(_SZ)], _I32),
+    "tr_vandermonde": ([_P, _I64, _P, _I32, _I64, _I32, _P, _I32, _P, _P, _P, _E], _I32),
 }
 
 
@@ -271,7 +271,16 @@ class BatchPlan:
             pass
 
 
-def tr_vandermonde(x: torch.Tensor, coef: torch.Tensor, y: torch.Tensor, precision: int, ex: tr_exec) -> None:
-    """Y = V(x) C: x (m,) f32, coef (deg+1, npoly) f32 row-major, y (m, npoly) f32."""
+def tr_vandermonde_workspace_size(m: int, npoly: int) -> int:
+    b = ctypes.c_size_t(0)
+    _check(lib().tr_vandermonde_workspace_size(m, npoly, ctypes.byref(b)))
+    return b.value
+
+
+def tr_vandermonde(x: torch.Tensor, coef: torch.Tensor, y: torch.Tensor | None, precision: int, ex: tr_exec,
+                   colsum=None, colmin=None, colmax=None) -> None:
+    """Y = V(x) C: x (m,) f32, coef (deg+1, npoly) f32 row-major, y (m, npoly) f32 / bf16 or None; optional
+    per-column sum / min / max (npoly f32 each)."""
+    yt = dtype_of(y) if y is not None else TR_NONE
     _check(lib().tr_vandermonde(_ptr(x), x.numel(), _ptr(coef), coef.shape[0] - 1, coef.shape[1], precision, _ptr(y),
-                                ctypes.byref(ex)))
+                                yt, _ptr(colsum), _ptr(colmin), _ptr(colmax), ctypes.byref(ex)))

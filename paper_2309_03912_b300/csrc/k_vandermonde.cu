@@ -1,35 +1,54 @@
 // k_vandermonde.cu -- tr_vandermonde: many polynomials at many points,
-// Y[i][j] = sum_k C[k][j] x_i^k, i.e. Y = V(x) C with V the Vandermonde matrix.
+// Y[i][j] = sum_k C[k][j] x_i^k, i.e. Y = V(x) C with V the Vandermonde matrix,
+// written out (FP32 or BF16) and/or reduced per column (polynomial) to its sum,
+// minimum and maximum over the points.
 //
-// TR_PREC_BF16X3 (tensor cores, tcgen05 + TMEM):
-//   Split-BF16 product in the manner of Henry, Tang & Heinecke, "Leveraging
-//   the bfloat16 artificial intelligence datatype for higher-precision
-//   computations" (ARITH 2019): V = Vh + Vl and C = Ch + Cl with bf16 parts,
-//   Y ~= Vh Ch + Vh Cl + Vl Ch accumulated in FP32 (the Vl Cl term is below
-//   FP32 resolution of the result and is dropped).
+// Split-BF16 on the tensor cores (tcgen05 + TMEM), in the manner of Henry,
+// Tang & Heinecke, "Leveraging the bfloat16 artificial intelligence datatype
+// for higher-precision computations" (ARITH 2019): every FP32 value v is
+// carried as bf16 parts v = v1 + v2 (+ v3), and the product keeps the terms
+// whose parts sum to at most the split's order -- bf16x3: V1C1 + V1C2 + V2C1
+// (about 2^-16 relative); bf16x6: also V1C3 + V2C2 + V3C1 (about FP32
+// accuracy) -- accumulated in FP32 in tensor memory.
 //   * A persistent grid (two CTAs per SM, 128 threads each) walks 128 x 256
 //     output tiles in column-tile-major order, so a CTA reloads its C tile
 //     only when the column tile changes.
 //   * V is never stored: each thread forms the 32 powers of its point in FP32
-//     and writes their bf16 high and low parts to shared memory in the
-//     tensor-core K-major core-matrix layout (8 rows x 16 bytes per core
+//     (zero above the degree) and writes their bf16 parts to shared memory in
+//     the tensor-core K-major core-matrix layout (8 rows x 16 bytes per core
 //     matrix; K-adjacent core matrices 128 B apart, 8-row groups 512 B apart).
-//   * One thread issues 6 tcgen05.mma (kind::f16, bf16 inputs, FP32
-//     accumulate, M = 128, N = 256, K = 16 each) into a 256-column TMEM
+//   * One thread issues the products' tcgen05.mma (kind::f16, bf16 inputs,
+//     FP32 accumulate, M = 128, N = 256, K = 16 each) into a 256-column TMEM
 //     accumulator and commits them to an mbarrier; the other CTA on the SM
 //     overlaps its own tile with this one.
 //   * The epilogue reads the accumulator with tcgen05.ld (32 lanes x 32
-//     columns per warp and step), stages each 32 x 32 block in shared memory
-//     in the 128-byte-swizzled layout and writes it with one 2-D TMA tensor
-//     store (bulk async-groups, two staging blocks per warp in rotation).
-//   Every mbarrier wait is bounded; on expiry the CTA records TR_ERR_TIMEOUT in
-//   the workspace, stops, and still frees its TMEM.
+//     columns per warp and step) and stages each 32 x 32 block in shared
+//     memory (128-byte swizzle), from where
+//       - FP32 Y leaves by one 2-D TMA tensor store (bulk async-groups, two
+//         staging blocks per warp in rotation; the tensor map clips rows and
+//         columns beyond m and npoly);
+//       - BF16 Y is rounded (nearest even) and leaves by coalesced 16-byte
+//         stores from a second, 64-byte-swizzled staging block;
+//       - the column reduction reads the block column-wise: each lane takes
+//         one column's 32 rows (conflict-free under the swizzle) and folds
+//         them into its running compensated sum, minimum and maximum, so one
+//         lane owns 8 of the tile's 256 columns across the CTA's row tiles.
+//     When the CTA's column tile changes, its four warps' running results are
+//     combined in FP64 and written to a workspace slot (CTA + column tile),
+//     and a second small kernel joins each column's slots in CTA order, in
+//     FP64: deterministic results.
+//   Every mbarrier wait is bounded by %globaltimer; on expiry the CTA records
+//   TR_ERR_TIMEOUT, waits once more (bounded) for the committed products to
+//   drain, stops, and still frees its TMEM.
 //
 // TR_PREC_FP32 (CUDA cores): the plain comparison -- one thread per
 // polynomial holding its coefficients in registers, FP32 Horner with fma over
 // a block of points, coalesced row stores.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
+#include "accum.cuh"
 #include "internal.h"
 
 namespace tr {
@@ -64,7 +83,7 @@ __global__ void __launch_bounds__(kF32Threads) k_vander_fp32(const float* __rest
   }
 }
 
-// ------------------------------------------------------------- tcgen05 bf16x3
+// ------------------------------------------------------------- tcgen05 split-bf16
 constexpr int kTcThreads = 128;
 constexpr int kTileM = 128, kTileN = 256, kK = 32;
 constexpr uint32_t kTmemCols = 256;
@@ -74,12 +93,38 @@ constexpr uint32_t kLBO = 128;   // between K-adjacent core matrices
 constexpr uint32_t kSBO = 512;   // between 8-row groups (K = 32: 4 core matrices)
 constexpr uint32_t kABytes = kTileM * kK * 2;  // 8 KiB per bf16 part
 constexpr uint32_t kBBytes = kTileN * kK * 2;  // 16 KiB per bf16 part
-constexpr uint32_t kStageBytes = 32 * 32 * 4;                  // one warp's 32 x 32 FP32 output block
-constexpr uint32_t kSmemUsed = 2 * kABytes + 2 * kBBytes + 4 * 2 * kStageBytes + 64;
-// request more dynamic shared memory than used so that at most two CTAs share
-// an SM: two 256-column accumulators fill the SM's 512 TMEM columns
-constexpr uint32_t kSmemRequest = 96 * 1024;
-constexpr long long kWaitLimit = 1ll << 26;  // mbarrier polls before giving up
+constexpr uint32_t kStageBytes = 32 * 32 * 4;  // one warp's 32 x 32 FP32 block
+constexpr uint32_t kStageBf16 = 32 * 32 * 2;   // the same in BF16
+constexpr uint64_t kMmaWaitNs = 1000000000ull; // 1 s for a tile's products
+constexpr int kMaxTcGrid = 512;                // workspace slots are sized for this many CTAs
+
+enum { kOutNone = 0, kOutF32 = 1, kOutBf16 = 2 };
+
+// Shared-memory layout of a CTA: NS A parts, NS B parts, FP32 staging (two
+// blocks per warp with a TMA output, one for a reduction without it), BF16
+// staging, mbarrier and TMEM slot.  The request is at least 80 KiB so that at
+// most two CTAs share an SM: two 256-column accumulators fill its 512 TMEM
+// columns.
+template <int NS, int OUT, bool RED>
+struct TcLayout {
+  static constexpr uint32_t a = 0;
+  static constexpr uint32_t b = NS * kABytes;
+  static constexpr uint32_t f32 = b + NS * kBBytes;
+  static constexpr uint32_t f32_bytes = OUT == kOutF32 ? 4 * 2 * kStageBytes : (RED ? 4 * kStageBytes : 0);
+  static constexpr uint32_t bf = f32 + f32_bytes;
+  static constexpr uint32_t bf_bytes = OUT == kOutBf16 ? 4 * kStageBf16 : 0;
+  static constexpr uint32_t bar = bf + bf_bytes;
+  static constexpr uint32_t used = bar + 64;
+  static constexpr uint32_t request = used + 1024 > 80 * 1024 ? used + 1024 : 80 * 1024;
+  static_assert(request <= 110 * 1024, "two CTAs per SM");
+  static_assert(!RED || f32_bytes >= 4 * 8 * 32 * 16, "room for the column combination");
+};
+
+// Per-column partial result of one CTA (one workspace slot entry).
+struct ColPart {
+  double sum;
+  float mn, mx;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -110,18 +155,6 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
   asm volatile(
@@ -137,6 +170,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 64 columns: lane l of the warp receives columns 0..63 of its TMEM lane.
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float* v) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,"
+      "%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+        "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Pack 8 floats as bf16 (round to nearest even).
 __device__ __forceinline__ uint4 pack_bf16x8(const float* v) {
   uint32_t w[4];
@@ -148,40 +202,55 @@ __device__ __forceinline__ uint4 pack_bf16x8(const float* v) {
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Split v into bf16 high part and bf16 remainder, both packed in K-major
-// core-matrix layout for row `r` of a tile starting at hi / lo.
-__device__ __forceinline__ void store_split_row(unsigned char* hi, unsigned char* lo, int r, const float* v) {
-  float h[kK], l[kK];
+// Split v into NS bf16 parts (v = p0 + p1 + ..., each remainder exact in FP32)
+// and store them in K-major core-matrix layout for row `r` of tiles starting at
+// part[0], part[0] + stride, ...
+template <int NS>
+__device__ __forceinline__ void store_split_row(unsigned char* part0, uint32_t stride, int r, const float* v) {
+  float rem[kK];
 #pragma unroll
-  for (int k = 0; k < kK; ++k) {
-    h[k] = __bfloat162float(__float2bfloat16_rn(v[k]));
-    l[k] = v[k] - h[k];  // exact in FP32
-  }
+  for (int k = 0; k < kK; ++k) rem[k] = v[k];
   const uint32_t row_off = (uint32_t)(r / 8) * kSBO + (uint32_t)(r % 8) * 16;
 #pragma unroll
-  for (int kc = 0; kc < kK / 8; ++kc) {
-    *reinterpret_cast<uint4*>(hi + row_off + kc * kLBO) = pack_bf16x8(h + 8 * kc);
-    *reinterpret_cast<uint4*>(lo + row_off + kc * kLBO) = pack_bf16x8(l + 8 * kc);
+  for (int p = 0; p < NS; ++p) {
+    float h[kK];
+#pragma unroll
+    for (int k = 0; k < kK; ++k) {
+      h[k] = __bfloat162float(__float2bfloat16_rn(rem[k]));
+      rem[k] = rem[k] - h[k];  // exact in FP32
+    }
+#pragma unroll
+    for (int kc = 0; kc < kK / 8; ++kc)
+      *reinterpret_cast<uint4*>(part0 + p * stride + row_off + kc * kLBO) = pack_bf16x8(h + 8 * kc);
   }
 }
 
+// The tile ranges of a CTA (contiguous, column-tile-major): [t_begin, t_end).
+__host__ __device__ __forceinline__ int64_t tc_tile_begin(int64_t tiles, int64_t cta, int64_t grid) {
+  return tiles * cta / grid;
+}
+
+template <int NS, int OUT, bool RED>
 __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_constant__ CUtensorMap ymap,
                                                              const float* __restrict__ x, int64_t m,
                                                              const float* __restrict__ coef, int deg, int64_t npoly,
+                                                             __nv_bfloat16* __restrict__ ybf, ColPart* parts,
                                                              WsHeader* hdr) {
+  using L = TcLayout<NS, OUT, RED>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
-  unsigned char* sAh = base;
-  unsigned char* sAl = sAh + kABytes;
-  unsigned char* sBh = sAl + kABytes;
-  unsigned char* sBl = sBh + kBBytes;
-  unsigned char* sOut = sBl + kBBytes;  // 4 warps x 2 staging blocks, 1024-byte aligned
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sOut + 4 * 2 * kStageBytes);
+  unsigned char* sA = base + L::a;
+  unsigned char* sB = base + L::b;
+  unsigned char* sF = base + L::f32;  // 1024-byte aligned (part sizes are multiples of 8 KiB)
+  unsigned char* sH = base + L::bf;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(base + L::bar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t m_tiles = m / kTileM, n_tiles = npoly / kTileN, tiles = m_tiles * n_tiles;
-  const int64_t t_begin = tiles * blockIdx.x / gridDim.x, t_end = tiles * (blockIdx.x + 1) / gridDim.x;
+  const int64_t m_tiles = (m + kTileM - 1) / kTileM, n_tiles = (npoly + kTileN - 1) / kTileN;
+  const int64_t tiles = m_tiles * n_tiles;
+  const int64_t t_begin = tc_tile_begin(tiles, blockIdx.x, gridDim.x),
+                t_end = tc_tile_begin(tiles, blockIdx.x + 1, gridDim.x);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -190,13 +259,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init(smem_u32(mbar), 1);
+    mbar_init_fence();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+
+  // running column results of this lane: column 32 c + lane of the current column tile, over
+  // the rows of this warp's 32 TMEM lanes of every row tile seen so far
+  float cs_hi[8], cs_lo[8], cmn[8], cmx[8];
+  auto reset_cols = [&]() {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) cs_hi[c] = cs_lo[c] = 0.0f, cmn[c] = INFINITY, cmx[c] = -INFINITY;
+  };
+  // the CTA's results for column tile nt into its workspace slot (CTA + nt): warps combined in
+  // FP64, in warp order, through the FP32 staging (every TMA store has finished reading it)
+  auto flush_cols = [&](int64_t nt) {
+    if constexpr (OUT == kOutF32) {
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+    __syncthreads();
+    ColPart* cp = reinterpret_cast<ColPart*>(sF);  // [warp][c][lane]
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      cp[(warp * 8 + c) * 32 + lane] = ColPart{(double)cs_hi[c] + (double)cs_lo[c], cmn[c], cmx[c]};
+    __syncthreads();
+    ColPart* slot = parts + (blockIdx.x + nt) * kTileN;
+    for (int col = tid; col < kTileN; col += kTcThreads) {
+      const int c = col / 32, l = col % 32;
+      double sum = 0.0;
+      float mn = INFINITY, mx = -INFINITY;
+      for (int w = 0; w < 4; ++w) {
+        const ColPart q = cp[(w * 8 + c) * 32 + l];
+        sum += q.sum;
+        mn = fminf(mn, q.mn);
+        mx = fmaxf(mx, q.mx);
+      }
+      slot[col] = ColPart{sum, mn, mx};
+    }
+    __syncthreads();
+    reset_cols();
+  };
+  if constexpr (RED) reset_cols();
 
   uint32_t phase = 0;
   int64_t loaded_n = -1;
@@ -204,45 +310,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
   for (int64_t t = t_begin; t < t_end && ok; ++t) {
     const int64_t nt = t / m_tiles, mt = t % m_tiles;
     const int64_t m0 = mt * kTileM, n0 = nt * kTileN;
-    if (nt != loaded_n) {  // C tile: columns n0 .. n0+255, powers 0 .. 31 (zero beyond deg)
+    if (nt != loaded_n) {
+      if constexpr (RED) {
+        if (loaded_n >= 0) flush_cols(loaded_n);
+      }
+      // C tile: columns n0 .. n0+255 (zero beyond npoly), powers 0 .. 31 (zero beyond deg)
       for (int half = 0; half < 2; ++half) {
         const int r = tid + half * kTcThreads;
+        const bool in = n0 + r < npoly;
         float v[kK];
 #pragma unroll
-        for (int k = 0; k < kK; ++k) v[k] = (k <= deg) ? __ldg(&coef[(int64_t)k * npoly + n0 + r]) : 0.0f;
-        store_split_row(sBh, sBl, r, v);
+        for (int k = 0; k < kK; ++k) v[k] = (in && k <= deg) ? __ldg(&coef[(int64_t)k * npoly + n0 + r]) : 0.0f;
+        store_split_row<NS>(sB, kBBytes, r, v);
       }
       loaded_n = nt;
     }
-    {  // V tile: the 32 powers of point m0 + tid, by repeated FP32 multiplication
-      const float xi = __ldg(&x[m0 + tid]);
+    {  // V tile: the powers of point m0 + tid by repeated FP32 multiplication, zero above deg
+      const float xi = m0 + tid < m ? __ldg(&x[m0 + tid]) : 0.0f;
       float v[kK];
       v[0] = 1.0f;
 #pragma unroll
-      for (int k = 1; k < kK; ++k) v[k] = v[k - 1] * xi;
-      store_split_row(sAh, sAl, tid, v);
+      for (int k = 1; k < kK; ++k) v[k] = k <= deg ? v[k - 1] * xi : 0.0f;
+      store_split_row<NS>(sA, kABytes, tid, v);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic-proxy smem writes -> tensor core
+    fence_async_smem();  // generic-proxy smem writes -> tensor core
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ah = smem_u32(sAh), al = smem_u32(sAl), bh = smem_u32(sBh), bl = smem_u32(sBl);
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      // the products V_i C_j with i + j <= NS - 1 (parts numbered from 0), largest first;
+      // K = 16 per instruction: two steps of two core matrices each
+      bool first = true;
 #pragma unroll
-      for (int s = 0; s < 2; ++s)  // K = 16 per instruction: skip two core matrices per step
-        mma_bf16(tmem, smem_desc(ah + s * 2 * kLBO), smem_desc(bh + s * 2 * kLBO), s > 0 ? 1u : 0u);
+      for (int d = 0; d < NS; ++d)
 #pragma unroll
-      for (int s = 0; s < 2; ++s) mma_bf16(tmem, smem_desc(ah + s * 2 * kLBO), smem_desc(bl + s * 2 * kLBO), 1u);
+        for (int i = 0; i <= d; ++i) {
+          const uint32_t ai = a0 + i * kABytes, bj = b0 + (d - i) * kBBytes;
 #pragma unroll
-      for (int s = 0; s < 2; ++s) mma_bf16(tmem, smem_desc(al + s * 2 * kLBO), smem_desc(bh + s * 2 * kLBO), 1u);
+          for (int s = 0; s < 2; ++s) {
+            mma_bf16(tmem, smem_desc(ai + s * 2 * kLBO), smem_desc(bj + s * 2 * kLBO), first ? 0u : 1u);
+            first = false;
+          }
+        }
       mma_commit(smem_u32(mbar));
     }
-    long long polls = 0;
-    while (!mbar_try_wait(smem_u32(mbar), phase)) {
-      if (++polls > kWaitLimit) {
-        ok = false;
-        break;
-      }
-    }
+    if (!mbar_wait_until(smem_u32(mbar), phase, kMmaWaitNs)) ok = false;
     phase ^= 1u;
     if (!__syncthreads_and(ok ? 1 : 0)) {
       ok = false;
@@ -250,39 +362,174 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31.  Each 32 x 32 block goes
-    // registers -> swizzled shared staging (row r's 16-byte chunk q at q ^ (r % 8), the
-    // 128-byte swizzle of the tensor map) -> one TMA tensor store issued by lane 0.
-    // Two staging blocks per warp alternate; lane 0 waits until the store issued two
-    // blocks earlier has finished reading its block before it is overwritten.
-#pragma unroll 1
-    for (int c = 0; c < kTileN / 32; ++c) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-      unsigned char* stg = sOut + (uint32_t)(warp * 2 + (c & 1)) * kStageBytes;
-      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-      __syncwarp();
+    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31; 64 columns per TMEM load, handled as
+    // two 32 x 32 blocks; the steps are unrolled so that the running column results stay in
+    // registers and the blocks' dependency chains overlap
+    const int64_t row0 = m0 + warp * 32;
+    const int valid_rows = (int)imax<int64_t>(0, imin<int64_t>(32, m - row0));
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        *reinterpret_cast<uint4*>(stg + lane * 128 + ((q ^ (lane & 7)) * 16)) = pack16(v + 4 * q);
-      fence_async_smem();
-      __syncwarp();
-      if (lane == 0) {
-        asm volatile(
-            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(&ymap),
-            "r"((int)(n0 + c * 32)), "r"((int)(m0 + warp * 32)), "r"(smem_u32(stg))
-            : "memory");
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    for (int cp = 0; cp < kTileN / 64; ++cp) {
+      float v64[64];
+      tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cp * 64), v64);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * cp + h;
+        const float* v = v64 + 32 * h;
+        const int64_t col0 = n0 + c * 32;
+        if constexpr (OUT == kOutF32 || RED) {
+          // row `lane`'s 16-byte chunk q at chunk q ^ (lane % 8): the 128-byte swizzle of the tensor map
+          unsigned char* stg = sF + (uint32_t)(OUT == kOutF32 ? warp * 2 + (c & 1) : warp) * kStageBytes;
+          if (OUT == kOutF32 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<uint4*>(stg + lane * 128 + ((q ^ (lane & 7)) * 16)) = pack16(v + 4 * q);
+          if constexpr (OUT == kOutF32) {
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              if (valid_rows > 0 && col0 < npoly)
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(&ymap),
+                    "r"((int)col0), "r"((int)row0), "r"(smem_u32(stg))
+                    : "memory");
+              // one bulk group per block even when the store is skipped (an empty group), so that
+              // "at most one group pending" always means the staging slot written next is free
+              asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+          } else {
+            __syncwarp();
+          }
+          if constexpr (RED) {
+            // column `lane` of the block, rows 0..31: element (r, lane) at
+            // r * 128 + ((lane / 4) ^ (r % 8)) * 16 + (lane % 4) * 4 (one bank per lane)
+            const float* colp = reinterpret_cast<const float*>(stg);
+            float e[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) e[r] = colp[r * 32 + (((lane >> 2) ^ (r & 7)) << 2) + (lane & 3)];
+            float tmn, tmx;
+            if (valid_rows == 32) {
+              tmn = min3f(e[0], e[1], e[2]);
+              tmx = max3f(e[0], e[1], e[2]);
+#pragma unroll
+              for (int r = 3; r + 1 < 32; r += 2) {
+                tmn = min3f(tmn, e[r], e[r + 1]);
+                tmx = max3f(tmx, e[r], e[r + 1]);
+              }
+              tmn = fminf(tmn, e[31]);
+              tmx = fmaxf(tmx, e[31]);
+            } else {  // the last row tile: rows beyond m are left out
+              tmn = INFINITY;
+              tmx = -INFINITY;
+#pragma unroll
+              for (int r = 0; r < 32; ++r) {
+                const bool in = r < valid_rows;
+                tmn = fminf(tmn, in ? e[r] : INFINITY);
+                tmx = fmaxf(tmx, in ? e[r] : -INFINITY);
+                e[r] = in ? e[r] : 0.0f;
+              }
+            }
+            const float ts = pairwise<32>(e);
+            // compensated running sum (Kahan) of the per-tile partial sums
+            const float yk = ts - (-cs_lo[c]);
+            const float tt = cs_hi[c] + yk;
+            cs_lo[c] = -((tt - cs_hi[c]) - yk);
+            cs_hi[c] = tt;
+            cmn[c] = fminf(cmn[c], tmn);
+            cmx[c] = fmaxf(cmx[c], tmx);
+          }
+        }
+        if constexpr (OUT == kOutBf16) {
+          // row `lane`'s four 16-byte chunks (8 bf16 each) at chunk q ^ ((lane / 2) % 4)
+          // (64-byte rows, conflict-free writes); then 8 rows per instruction leave as 16-byte stores
+          unsigned char* hb = sH + (uint32_t)warp * kStageBf16;
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint4*>(hb + lane * 64 + ((q ^ ((lane >> 1) & 3)) * 16)) = pack_bf16x8(v + 8 * q);
+          __syncwarp();
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = i * 8 + (lane >> 2), q = lane & 3;
+            const uint4 w = *reinterpret_cast<const uint4*>(hb + r * 64 + ((q ^ ((r >> 1) & 3)) * 16));
+            const int64_t col = col0 + q * 8;
+            if (r < valid_rows && col < npoly) st_stream(ybf + (row0 + r) * npoly + col, w);
+          }
+        }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();  // TMEM and the A / B tiles are free for the next tile
   }
-  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // this warp's stores are done
+  if constexpr (RED) {
+    if (ok && loaded_n >= 0) flush_cols(loaded_n);
+  }
+  if (!ok) mbar_wait_until(smem_u32(mbar), phase ^ 1u, kMmaWaitNs);  // let committed products drain
+  if (OUT == kOutF32 && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // stores done
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// Second launch of the column reduction: thread j joins column j's slots in CTA
+// order (the CTAs whose tile range meets column tile j / 256), in FP64.
+__global__ void __launch_bounds__(256) k_vander_cols(const ColPart* __restrict__ parts, int64_t m_tiles,
+                                                     int64_t tiles, int64_t grid, int64_t npoly, float* colsum,
+                                                     float* colmin, float* colmax) {
+  const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (j >= npoly) return;
+  const int64_t nt = j / kTileN, lo = nt * m_tiles, hi = lo + m_tiles;
+  double sum = 0.0;
+  float mn = INFINITY, mx = -INFINITY;
+  for (int64_t c = 0; c < grid; ++c) {
+    const int64_t tb = tc_tile_begin(tiles, c, grid), te = tc_tile_begin(tiles, c + 1, grid);
+    if (te <= lo || tb >= hi || tb == te) continue;
+    const ColPart q = parts[(c + nt) * kTileN + j % kTileN];
+    sum += q.sum;
+    mn = fminf(mn, q.mn);
+    mx = fmaxf(mx, q.mx);
+  }
+  if (colsum) colsum[j] = (float)sum;
+  if (colmin) colmin[j] = mn;
+  if (colmax) colmax[j] = mx;
+}
+
+template <int NS, int OUT, bool RED>
+tr_status launch_tc(const CUtensorMap& ymap, const float* x, int64_t m, const float* coef, int deg, int64_t npoly,
+                    void* y, float* colsum, float* colmin, float* colmax, const tr_exec* e) {
+  using L = TcLayout<NS, OUT, RED>;
+  auto kern = k_vander_tc<NS, OUT, RED>;
+  tr_status s = ensure_dyn_smem((const void*)kern, (int)L::request, "cudaFuncSetAttribute(k_vander_tc)");
+  if (s) return s;
+  const int64_t m_tiles = ceil_div(m, kTileM), tiles = m_tiles * ceil_div(npoly, kTileN);
+  const int64_t grid = std::min<int64_t>(std::min<int64_t>(tiles, 2 * (int64_t)dev_info().sm_count), kMaxTcGrid);
+  ColPart* parts = reinterpret_cast<ColPart*>(ws_body(e));
+  cudaStream_t st = stream_of(e);
+  kern<<<(unsigned)grid, kTcThreads, L::request, st>>>(ymap, x, m, coef, deg, npoly,
+                                                       static_cast<__nv_bfloat16*>(y), parts, ws_header(e));
+  if ((s = launch_status("k_vander_tc"))) return s;
+  if constexpr (RED) {
+    k_vander_cols<<<(unsigned)ceil_div(npoly, 256), 256, 0, st>>>(parts, m_tiles, tiles, grid, npoly, colsum, colmin,
+                                                                 colmax);
+    return launch_status("k_vander_cols");
+  }
+  return TR_OK;
+}
+
+template <int NS>
+tr_status launch_tc_ns(int out, bool red, const CUtensorMap& ymap, const float* x, int64_t m, const float* coef,
+                       int deg, int64_t npoly, void* y, float* cs, float* cn, float* cx, const tr_exec* e) {
+  if (out == kOutF32) return red ? launch_tc<NS, kOutF32, true>(ymap, x, m, coef, deg, npoly, y, cs, cn, cx, e)
+                                 : launch_tc<NS, kOutF32, false>(ymap, x, m, coef, deg, npoly, y, cs, cn, cx, e);
+  if (out == kOutBf16) return red ? launch_tc<NS, kOutBf16, true>(ymap, x, m, coef, deg, npoly, y, cs, cn, cx, e)
+                                  : launch_tc<NS, kOutBf16, false>(ymap, x, m, coef, deg, npoly, y, cs, cn, cx, e);
+  return launch_tc<NS, kOutNone, true>(ymap, x, m, coef, deg, npoly, y, cs, cn, cx, e);
+}
+
+size_t vander_ws_bytes(int64_t npoly) {
+  return (size_t)kWsHeader + (size_t)(kMaxTcGrid + ceil_div(std::max<int64_t>(npoly, 1), kTileN)) * kTileN *
+                                 sizeof(ColPart);
 }
 
 }  // namespace
@@ -293,48 +540,58 @@ using namespace tr;
 
 extern "C" {
 
-tr_status tr_vandermonde_workspace_size(size_t* bytes) {
-  if (!bytes) return fail(TR_ERR_INVALID_ARG, "bytes is NULL");
-  *bytes = kWsHeader;
+tr_status tr_vandermonde_workspace_size(int64_t m, int64_t npoly, size_t* bytes) {
+  if (!bytes || m < 0 || npoly < 0) return fail(TR_ERR_INVALID_ARG, "bad arguments");
+  *bytes = vander_ws_bytes(npoly);
   return TR_OK;
 }
 
 tr_status tr_vandermonde(const float* x, int64_t m, const float* coef, int32_t deg, int64_t npoly, int precision,
-                         float* y, const tr_exec* e) {
+                         void* y, tr_dtype yt, float* colsum, float* colmin, float* colmax, const tr_exec* e) {
   if (!e) return fail(TR_ERR_INVALID_ARG, "exec is NULL");
   if (m < 0 || npoly < 0) return fail(TR_ERR_INVALID_ARG, "m or npoly < 0");
   if (deg < 0 || deg > TR_MAX_DEGREE) return fail(TR_ERR_INVALID_ARG, "degree %d out of [0, %d]", deg, TR_MAX_DEGREE);
-  if (precision != TR_PREC_BF16X3 && precision != TR_PREC_FP32) return fail(TR_ERR_INVALID_ARG, "precision %d", precision);
-  if (m > 0 && npoly > 0 && (!x || !coef || !y)) return fail(TR_ERR_INVALID_ARG, "x, coef or y is NULL");
-  if ((x && !aligned_to(x, 4)) || (coef && !aligned_to(coef, 4)) || (y && !aligned_to(y, 4)))
-    return fail(TR_ERR_ALIGNMENT, "pointers must be 4-byte aligned");
-  if (m == 0 || npoly == 0) return TR_OK;
+  if (precision != TR_PREC_BF16X3 && precision != TR_PREC_FP32 && precision != TR_PREC_BF16X6)
+    return fail(TR_ERR_INVALID_ARG, "precision %d", precision);
+  if (yt != TR_F32 && yt != TR_BF16 && yt != TR_NONE) return fail(TR_ERR_UNSUPPORTED, "output dtype %d", yt);
+  const bool red = colsum || colmin || colmax;
+  if (yt == TR_NONE && !red) return fail(TR_ERR_INVALID_ARG, "no output requested (y and column results)");
+  if (m > 0 && npoly > 0 && (!x || !coef || (yt != TR_NONE && !y)))
+    return fail(TR_ERR_INVALID_ARG, "x, coef or y is NULL");
+  if ((x && !aligned_to(x, 4)) || (coef && !aligned_to(coef, 4)) || (y && !aligned_to(y, yt == TR_BF16 ? 2 : 4)) ||
+      (colsum && !aligned_to(colsum, 4)) || (colmin && !aligned_to(colmin, 4)) || (colmax && !aligned_to(colmax, 4)))
+    return fail(TR_ERR_ALIGNMENT, "pointers must be aligned to their element size");
+  if (m > 0x7FFFFFFF || npoly > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "m or npoly beyond 32-bit coordinates");
   cudaStream_t st = stream_of(e);
   if (precision == TR_PREC_FP32) {
+    if (yt != TR_F32 || red)
+      return fail(TR_ERR_UNSUPPORTED, "the FP32 Horner path writes FP32 Y only (no BF16 or column results)");
+    if (m == 0 || npoly == 0) return TR_OK;
     if (ceil_div(npoly, kF32Threads) > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "npoly too large");
     const dim3 grid((unsigned)ceil_div(npoly, kF32Threads), (unsigned)std::min<int64_t>(ceil_div(m, kF32Points), 65535));
-    k_vander_fp32<<<grid, kF32Threads, 0, st>>>(x, m, coef, deg, npoly, y);
+    k_vander_fp32<<<grid, kF32Threads, 0, st>>>(x, m, coef, deg, npoly, static_cast<float*>(y));
     return launch_status("k_vander_fp32");
   }
-  if (m % kTileM || npoly % kTileN)
-    return fail(TR_ERR_UNSUPPORTED, "bf16x3 tensor path needs m %% %d == 0 and npoly %% %d == 0", kTileM, kTileN);
-  if (!aligned_to(y, 16)) return fail(TR_ERR_ALIGNMENT, "y must be 16-byte aligned for the tensor path");
-  if (!e->workspace || e->workspace_bytes < (size_t)kWsHeader)
-    return fail(TR_ERR_WORKSPACE, "the tensor path needs a %d-byte workspace (status word)", kWsHeader);
-  static_assert(kSmemUsed + 1024 <= kSmemRequest, "shared memory budget");
-  tr_status s = cuda_status(
-      cudaFuncSetAttribute(k_vander_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemRequest),
-      "cudaFuncSetAttribute(k_vander_tc)");
-  if (s) return s;
-  if (m > 0x7FFFFFFF || npoly > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "m or npoly beyond 32-bit coordinates");
+  if (yt == TR_F32 && (npoly % 4 || !aligned_to(y, 16)))
+    return fail(TR_ERR_ALIGNMENT, "FP32 output on the tensor path needs npoly %% 4 == 0 and a 16-byte aligned y");
+  if (yt == TR_BF16 && (npoly % 8 || !aligned_to(y, 16)))
+    return fail(TR_ERR_ALIGNMENT, "BF16 output on the tensor path needs npoly %% 8 == 0 and a 16-byte aligned y");
+  const size_t need = vander_ws_bytes(npoly);
+  if (!e->workspace || e->workspace_bytes < need)
+    return fail(TR_ERR_WORKSPACE, "the tensor path needs a %zu-byte workspace", need);
+  if (!aligned_to(e->workspace, 256)) return fail(TR_ERR_ALIGNMENT, "workspace must be 256-byte aligned");
+  if (m == 0 || npoly == 0) return TR_OK;
   CUtensorMap ymap;
-  if ((s = make_tensor_map_2d(&ymap, y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (uint64_t)npoly, (uint64_t)m,
+  std::memset(&ymap, 0, sizeof(ymap));
+  tr_status s;
+  if (yt == TR_F32 &&
+      (s = make_tensor_map_2d(&ymap, y, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (uint64_t)npoly, (uint64_t)m,
                               (uint64_t)npoly * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B)))
     return s;
-  const int64_t tiles = (m / kTileM) * (npoly / kTileN);
-  const int64_t grid = std::min<int64_t>(tiles, 2 * (int64_t)dev_info().sm_count);
-  k_vander_tc<<<(unsigned)grid, kTcThreads, kSmemRequest, st>>>(ymap, x, m, coef, deg, npoly, ws_header(e));
-  return launch_status("k_vander_tc");
+  const int out = yt == TR_F32 ? kOutF32 : (yt == TR_BF16 ? kOutBf16 : kOutNone);
+  return precision == TR_PREC_BF16X6
+             ? launch_tc_ns<3>(out, red, ymap, x, m, coef, deg, npoly, y, colsum, colmin, colmax, e)
+             : launch_tc_ns<2>(out, red, ymap, x, m, coef, deg, npoly, y, colsum, colmin, colmax, e);
 }
 
 }  // extern "C"

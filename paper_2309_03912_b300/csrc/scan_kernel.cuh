@@ -1,0 +1,658 @@
+// scan_kernel.cuh -- the kernel of tr_scan / tr_scan_reduce, prefix sums of f(x)
+// in one pass, as a template over the storage type, the map, the output
+// arithmetic and the map's source (the family's MapParams, or a user-supplied
+// functor passed by value), with its launcher.
+//
+// Single-pass scan with decoupled look-back (Merrill & Garland, "Single-pass
+// parallel prefix scan with decoupled look-back", NVR-2016-002):
+//   * each block takes a tile id from an atomic counter (dynamic ids: every
+//     tile's predecessors have already started, so waiting on them ends);
+//   * lanes load consecutive 128-bit vectors of the tile (coalesced), map
+//     them and park the values in shared memory, one padded row of kItems
+//     contiguous elements per thread; threads total their rows, warps scan the
+//     totals with shuffles and the block combines warp totals;
+//   * the tile publishes its aggregate (flag A), then warp 0 looks back over
+//     32 (128 for u64 carries) predecessors per round,
+//     summing aggregates until it meets an inclusive prefix (flag P), and
+//     publishes its own inclusive prefix.  Each tile's state has its own
+//     128-byte line; u32 and FP64 carries share one 64-bit status word with
+//     their flag (one relaxed load, no fence), a u64 carry sits beside a flag
+//     released after it;
+//   * every wait is bounded by a %globaltimer deadline and an abort word: on
+//     expiry the block records TR_ERR_TIMEOUT and finishes instead of hanging.
+// Each call clears the look-back lines and the tile counter with two memsets
+// on the stream (graph-capturable) before the kernel.
+//
+// Arithmetic: u32 wraps modulo 2^32; u32 -> u64 is exact; float scans keep
+// float-float (hi, lo) pairs inside a tile, FP64 between tiles, and round each
+// output once from the compensated prefix.
+#pragma once
+
+#include "internal.h"
+
+namespace tr {
+namespace scank {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 32;
+constexpr int kTile = kThreads * kItems;  // 8192 elements
+
+constexpr uint32_t kFlagA = 1, kFlagP = 2;
+
+// ---- per-output arithmetic -------------------------------------------------
+struct OpU32 {
+  using T = uint32_t;      // in-tile running value
+  using Carry = uint32_t;  // between tiles
+  using Out = uint32_t;
+  __device__ static T zero() { return 0u; }
+  __device__ static T lift(uint32_t v) { return v; }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static Carry to_carry(T a) { return a; }
+  __device__ static Carry cadd(Carry a, Carry b) { return a + b; }
+  __device__ static T shfl_up(T a, int d) { return __shfl_up_sync(kFull, a, d); }
+  __device__ static Carry shfl_xor_c(Carry a, int d) { return __shfl_xor_sync(kFull, a, d); }
+};
+
+struct OpU64 {
+  using T = unsigned long long;
+  using Carry = unsigned long long;
+  using Out = unsigned long long;
+  __device__ static T zero() { return 0ull; }
+  __device__ static T lift(uint32_t v) { return v; }
+  __device__ static T add(T a, T b) { return a + b; }
+  __device__ static Carry to_carry(T a) { return a; }
+  __device__ static Carry cadd(Carry a, Carry b) { return a + b; }
+  __device__ static T shfl_up(T a, int d) { return __shfl_up_sync(kFull, a, d); }
+  __device__ static Carry shfl_xor_c(Carry a, int d) { return __shfl_xor_sync(kFull, a, d); }
+};
+
+struct OpF32 {
+  using T = FF;
+  using Carry = double;
+  using Out = float;
+  __device__ static T zero() { return FF{0.f, 0.f}; }
+  __device__ static T add(T a, T b) { return ff_add(a, b); }
+  __device__ static Carry to_carry(T a) { return ff_to_double(a); }
+  __device__ static Carry cadd(Carry a, Carry b) { return a + b; }
+  __device__ static T shfl_up(T a, int d) { return FF{__shfl_up_sync(kFull, a.hi, d), __shfl_up_sync(kFull, a.lo, d)}; }
+  __device__ static Carry shfl_xor_c(Carry a, int d) { return __shfl_xor_sync(kFull, a, d); }
+};
+
+template <class Op>
+__device__ __forceinline__ typename Op::T warp_incl_scan(typename Op::T v, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const typename Op::T o = Op::shfl_up(v, d);
+    if (lane >= d) v = Op::add(o, v);
+  }
+  return v;
+}
+
+template <class Op>
+__device__ __forceinline__ typename Op::Carry warp_sum_carry(typename Op::Carry v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = Op::cadd(v, Op::shfl_xor_c(v, d));
+  return v;
+}
+
+// Look-back state: one 128-byte line per tile, so that the polls of hundreds
+// of waiting tiles spread over many L2 lines instead of hammering a few (with
+// the state packed contiguously the polls contended for a handful of lines and
+// the u32 scan ran 25 % slower).  Where the carry and its flag fit one 64-bit
+// status word, one relaxed load sees both and no fence is needed: a u32 carry
+// takes the high half and the flag the low bits; an FP64 carry (float scans)
+// gives up its two lowest significand bits to the flag, i.e. it is published
+// truncated to 51 bits (a relative change below 2^-50, far below the FP32
+// outputs' resolution).  A u64 carry sits in the same line (aggregate at byte
+// 8, inclusive prefix at byte 16) and its flag (byte 0) is released after it.
+constexpr int kLineBytes = 128;
+struct ScanWs {
+  unsigned char* lines;  // tiles x kLineBytes
+};
+
+template <class Op>
+constexpr bool kPackedStatus = !std::is_same<typename Op::Carry, unsigned long long>::value;
+
+template <class Op>
+__device__ __forceinline__ unsigned long long pack_status(typename Op::Carry v, uint32_t flag) {
+  if constexpr (std::is_same<typename Op::Carry, double>::value) {
+    return ((unsigned long long)__double_as_longlong(v) & ~3ull) | flag;
+  } else {
+    return ((unsigned long long)v << 32) | flag;
+  }
+}
+template <class Op>
+__device__ __forceinline__ typename Op::Carry status_value(unsigned long long w) {
+  if constexpr (std::is_same<typename Op::Carry, double>::value) {
+    return __longlong_as_double((long long)(w & ~3ull));
+  } else {
+    return (typename Op::Carry)(w >> 32);
+  }
+}
+
+__device__ __forceinline__ unsigned char* status_line(ScanWs ws, int64_t tile) {
+  return ws.lines + tile * kLineBytes;
+}
+
+template <class Op>
+__device__ __forceinline__ void publish(ScanWs ws, int64_t tile, uint32_t flag, typename Op::Carry v) {
+  unsigned char* line = status_line(ws, tile);
+  if constexpr (kPackedStatus<Op>) {
+    st_relaxed_u64(reinterpret_cast<unsigned long long*>(line), pack_status<Op>(v, flag));
+  } else {
+    *reinterpret_cast<typename Op::Carry*>(line + (flag == kFlagP ? 16 : 8)) = v;
+    st_release_u32(reinterpret_cast<uint32_t*>(line), flag);
+  }
+}
+
+// Decoupled look-back for `tile` by one warp (the caller's warp 0): publishes
+// the aggregate (flag A), then reads the nearest unread predecessors (32 or
+// 128 per round), summing aggregates until an inclusive prefix (flag P) bounds the sum,
+// and publishes its own inclusive prefix.  Returns the exclusive prefix in
+// every lane; sets `gave_up` (and the status word) when a wait runs past the
+// deadline or another block has aborted.
+template <class Op>
+__device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typename Op::Carry aggregate, ScanWs ws,
+                                                            WsHeader* hdr, uint64_t timeout_ns, bool stall, int lane,
+                                                            bool& gave_up) {
+  using Carry = typename Op::Carry;
+  // predecessors read per lane and round: one with packed status words, four
+  // (a 128-tile window) for u64 carries, whose rounds cost a fence and a
+  // second load
+  constexpr int kSlots = kPackedStatus<Op> ? 1 : 4;
+  Carry excl = Carry(0);
+  gave_up = false;
+  if (tile == 0) {
+    if (lane == 0 && !stall) publish<Op>(ws, 0, kFlagP, aggregate);
+    return excl;
+  }
+  if (lane == 0 && !stall) publish<Op>(ws, tile, kFlagA, aggregate);
+  const uint64_t deadline = globaltimer_ns() + timeout_ns;
+  int64_t pos = tile - 1;
+  while (true) {
+    // slot m of lane l reads the predecessor at distance 32 m + l from pos
+    uint32_t st[kSlots];
+    Carry val[kSlots];
+    int stop = 0;
+#pragma unroll
+    for (int m = 0; m < kSlots; ++m) {
+      st[m] = kFlagP;  // before tile 0: an inclusive prefix of 0
+      val[m] = Carry(0);
+    }
+    for (int polls = 0;; ++polls) {  // the window's loads are issued together; waits are bounded
+      bool pending = false;
+#pragma unroll
+      for (int m = 0; m < kSlots; ++m) {
+        const int64_t idx = pos - 32 * m - lane;
+        if (idx >= 0 && (polls == 0 || st[m] == 0)) {
+          const unsigned char* line = status_line(ws, idx);
+          if constexpr (kPackedStatus<Op>) {
+            const unsigned long long w = ld_relaxed_u64(reinterpret_cast<const unsigned long long*>(line));
+            st[m] = (uint32_t)w & 3u;
+            val[m] = status_value<Op>(w);
+          } else {
+            st[m] = ld_relaxed_u32(reinterpret_cast<const uint32_t*>(line)) & 3u;
+          }
+          pending |= st[m] == 0;
+        }
+      }
+      if (!pending) break;
+      if ((polls & 15) == 15 && (globaltimer_ns() > deadline || ld_relaxed_u32(&hdr->abort) != 0u)) {
+        stop = 1;
+        break;
+      }
+    }
+    if (__any_sync(kFull, stop)) {
+      if (lane == 0 && !ld_relaxed_u32(&hdr->abort)) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)tile);
+      gave_up = true;
+      return excl;
+    }
+    if constexpr (!kPackedStatus<Op>) {
+      fence_acq_rel_gpu();  // orders the value reads after the flags
+#pragma unroll
+      for (int m = 0; m < kSlots; ++m) {
+        const int64_t idx = pos - 32 * m - lane;
+        if (idx >= 0) val[m] = *reinterpret_cast<const Carry*>(status_line(ws, idx) + (st[m] == kFlagP ? 16 : 8));
+      }
+    }
+    // the nearest predecessor holding an inclusive prefix: everything up to it is summed
+    int first = 32 * kSlots;
+#pragma unroll
+    for (int m = kSlots - 1; m >= 0; --m) {
+      const unsigned pm = __ballot_sync(kFull, st[m] == kFlagP);
+      if (pm) first = 32 * m + __ffs(pm) - 1;
+    }
+    Carry part = Carry(0);
+#pragma unroll
+    for (int m = 0; m < kSlots; ++m)
+      if (32 * m + lane <= first) part = Op::cadd(part, val[m]);
+    excl = Op::cadd(excl, warp_sum_carry<Op>(part));
+    if (first < 32 * kSlots) break;
+    pos -= 32 * kSlots;
+  }
+  if (lane == 0 && !stall) publish<Op>(ws, tile, kFlagP, Op::cadd(excl, aggregate));
+  return excl;
+}
+
+// ---- reduction in the same pass (tr_scan_reduce) ---------------------------
+// min / max travel as order-preserving unsigned keys so that one unsigned
+// maximum serves both (the minimum as the maximum of complemented keys): float
+// keys flip the sign bit of non-negative values and every bit of negative ones;
+// u32 values are their own keys.  A zero word means "no value yet" for both
+// (no non-NaN float has key 0 or complemented key 0; for u32, 0 is the identity
+// of max and ~0 that of min), so the cleared header words are the identities.
+__device__ __forceinline__ uint32_t mm_key(float v) {
+  const uint32_t b = __float_as_uint(v);
+  return b ^ ((b >> 31) ? 0xFFFFFFFFu : 0x80000000u);
+}
+__device__ __forceinline__ uint32_t mm_key(uint32_t v) { return v; }
+__device__ __forceinline__ float mm_float(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k ^ 0x80000000u) : ~k);
+}
+__device__ __forceinline__ float mm_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ float mm_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ uint32_t mm_min(uint32_t a, uint32_t b) { return min(a, b); }
+__device__ __forceinline__ uint32_t mm_max(uint32_t a, uint32_t b) { return max(a, b); }
+template <class C>
+__device__ __forceinline__ C mm_lowest();
+template <>
+__device__ __forceinline__ float mm_lowest<float>() { return -INFINITY; }
+template <>
+__device__ __forceinline__ uint32_t mm_lowest<uint32_t>() { return 0u; }
+template <class C>
+__device__ __forceinline__ C mm_highest();
+template <>
+__device__ __forceinline__ float mm_highest<float>() { return INFINITY; }
+template <>
+__device__ __forceinline__ uint32_t mm_highest<uint32_t>() { return 0xFFFFFFFFu; }
+
+__device__ __forceinline__ void red_max_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.max.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_release_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The reduction outputs of a scan (ops = 0: plain scan).
+struct ScanRed {
+  void* sum;
+  void* mn;
+  void* mx;
+  int32_t sum_t;  // tr_dtype
+  uint32_t ops;
+};
+
+// Run by thread 0 of the last tile after its look-back: `total` is the sum of f
+// over all tiles (without the carry-in).  The sum is written at once; min and
+// max once every tile has folded its own in (its count is released after its
+// folds), with the wait bounded like the look-back's.
+template <class Op, class C>
+__device__ __noinline__ void finish_reduction(const ScanRed& red, WsHeader* hdr, typename Op::Carry total,
+                                              uint32_t tiles, uint64_t timeout_ns) {
+  if ((red.ops & TR_SUM) && red.sum) {
+    if constexpr (std::is_same<Op, OpF32>::value) {
+      if (red.sum_t == TR_F64)
+        *static_cast<double*>(red.sum) = total;
+      else
+        *static_cast<float*>(red.sum) = (float)total;
+    } else if constexpr (std::is_same<Op, OpU64>::value) {
+      *static_cast<unsigned long long*>(red.sum) = total;
+    } else {
+      *static_cast<uint32_t*>(red.sum) = total;
+    }
+  }
+  if (!(red.ops & (TR_MIN | TR_MAX))) return;
+  const uint64_t deadline = globaltimer_ns() + timeout_ns;
+  for (int polls = 0; ld_acquire_u32(&hdr->red_done) < tiles; ++polls) {
+    if ((polls & 15) == 15 && (globaltimer_ns() > deadline || ld_relaxed_u32(&hdr->abort) != 0u)) {
+      if (!ld_relaxed_u32(&hdr->abort)) set_status(hdr, TR_ERR_TIMEOUT, tiles);
+      return;
+    }
+  }
+  const uint32_t kmn = ld_relaxed_u32(&hdr->red_min), kmx = ld_relaxed_u32(&hdr->red_max);
+  if constexpr (std::is_same<C, float>::value) {
+    if ((red.ops & TR_MIN) && red.mn) *static_cast<float*>(red.mn) = kmn ? mm_float(~kmn) : INFINITY;
+    if ((red.ops & TR_MAX) && red.mx) *static_cast<float*>(red.mx) = kmx ? mm_float(kmx) : -INFINITY;
+  } else {
+    if ((red.ops & TR_MIN) && red.mn) *static_cast<uint32_t*>(red.mn) = ~kmn;
+    if ((red.ops & TR_MAX) && red.mx) *static_cast<uint32_t*>(red.mx) = kmx;
+  }
+}
+
+// ---- the pipelined tile loop --------------------------------------------------
+//
+// A block is 8 compute warps plus one look-back warp and stays resident,
+// taking tile ids from the counter one ahead of use.  Per tile i the compute
+// warps map it into a padded row buffer (one of two), total the rows, hand
+// the tile's aggregate to the look-back warp, then -- while that warp resolves
+// tile i's prefix -- fetch tile i+1's vectors into registers and write tile
+// i-1's outputs, whose prefix the look-back warp delivered meanwhile.  So the
+// compute warps never wait out a look-back of their own tile, the loads of one
+// tile overlap the stores of another, and two tiles per block are in flight.
+// Hand-overs use named barriers, two per direction (by tile parity) so that a
+// barrier is never arrived at twice within one phase:
+//   kBarAgg + (i & 1)  compute warps arrive after publishing tile i's
+//                      aggregate; the look-back warp waits on it;
+//   kBarExcl + (i & 1) the look-back warp arrives after publishing tile i's
+//                      exclusive prefix; the compute warps wait on it before
+//                      writing tile i's outputs (one iteration later).
+// The look-back warp stops on a tile id of -1.
+constexpr int kBlockThreads = kThreads + 32;
+constexpr int kBarCompute = 1, kBarAgg = 2, kBarExcl = 4;
+
+__device__ __forceinline__ void bar_sync_n(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive_n(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void compute_sync() { bar_sync_n(kBarCompute, kThreads); }
+
+// Blocks per SM: two (each with two 33 KiB row buffers and 9 warps).  Measured
+// on B300 at 2^28 (u32 splitmix32 / f32 x^2): two blocks 447 / 520 us, three
+// blocks (72 registers, spilling) 532 / 605 us; one tile per block with six
+// blocks per SM and the look-back in warp 0, 460 / 550 us.
+constexpr int kBlocksPerSm = 2;
+
+// One item into a running in-tile value (TwoSum into (hi, lo) for floats).
+template <class Op, class C>
+__device__ __forceinline__ void run_add(typename Op::T& run, C v) {
+  if constexpr (std::is_same<Op, OpF32>::value) {
+    float sm, e;
+    two_sum(run.hi, v, sm, e);
+    run.hi = sm;
+    run.lo += e;
+  } else {
+    run = Op::add(run, Op::lift(v));
+  }
+}
+template <class Op>
+__device__ __forceinline__ typename Op::Out run_out(const typename Op::T& run) {
+  if constexpr (std::is_same<Op, OpF32>::value) {
+    return run.hi + run.lo;  // the compensated prefix, rounded once
+  } else {
+    return run;
+  }
+}
+
+// Lane totals warp-scanned; block totals in shared memory (compute warps only).
+template <class Op>
+__device__ __forceinline__ void block_totals(typename Op::T acc, typename Op::T* s_warp, typename Op::T& warp_off,
+                                             typename Op::T& excl_lane, typename Op::T& tile_tot) {
+  using T = typename Op::T;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const T incl_lane = warp_incl_scan<Op>(acc, lane);
+  excl_lane = Op::shfl_up(incl_lane, 1);
+  if (lane == 0) excl_lane = Op::zero();
+  if (lane == 31) s_warp[wid] = incl_lane;
+  compute_sync();
+  warp_off = Op::zero();
+  tile_tot = Op::zero();
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    if (w < wid) warp_off = Op::add(warp_off, s_warp[w]);
+    tile_tot = Op::add(tile_tot, s_warp[w]);
+  }
+}
+
+// Tiles move through shared memory in both directions so that every global
+// access is a coalesced 16-byte-per-lane access: lanes load consecutive
+// vectors, map them and scatter the values into per-thread rows (thread t owns
+// the kItems contiguous elements t*kItems...; rows padded to kItems + 1 words,
+// which makes the scatter, the row reads and the final gather free of bank
+// conflicts).  For the outputs each thread scans its row on top of its prefix
+// in place (outputs of 4 bytes) and the block stores the rows back out as
+// coalesced vectors; 8-byte outputs are stored from the thread's registers.
+constexpr int kRow = kItems + 1;  // padded row, in 4-byte words
+constexpr size_t kRowsBytes = (size_t)kThreads * kRow * 4;  // one row buffer
+constexpr size_t kDynBytes = 2 * kRowsBytes;                 // dynamic shared memory per block
+
+template <class In, class F, class Op, class Src>
+__global__ void __launch_bounds__(kBlockThreads, kBlocksPerSm)
+    k_scan(const In* __restrict__ x, typename Op::Out* y, int64_t n, int vec_ok, const __grid_constant__ Src P,
+           WsHeader* hdr, ScanWs ws, const typename Op::Out* carry_in, uint64_t timeout_ns, int64_t stall_tile,
+           int exclusive, ScanRed red, int64_t tiles) {
+  using S = Storage<In>;
+  using C = typename S::C;
+  using T = typename Op::T;
+  using Carry = typename Op::Carry;
+  using Out = typename Op::Out;
+  static_assert(sizeof(C) == 4, "4-byte compute values");
+  constexpr int V = S::kVec;
+  constexpr int kVecs = kTile / V;  // input vectors per tile
+  constexpr int kLoads = kVecs / kThreads;
+
+  __shared__ int64_t s_tile_of[2];  // tile handed to the look-back warp, by parity (-1: stop)
+  __shared__ Carry s_agg[2], s_excl[2];
+  __shared__ uint32_t s_next;
+  __shared__ T s_warp[kWarps];
+  __shared__ C s_mn[kWarps], s_mx[kWarps];
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  const int tid = threadIdx.x, lane = tid & 31;
+
+  if (tid >= kThreads) {  // ---- the look-back warp
+    for (int i = 0;; ++i) {
+      bar_sync_n(kBarAgg + (i & 1), kBlockThreads);
+      const int64_t tile = s_tile_of[i & 1];
+      if (tile < 0) break;
+      const Carry agg = s_agg[i & 1];
+      bool gave_up;
+      const Carry e = warp_lookback<Op>(tile, agg, ws, hdr, timeout_ns, tile == stall_tile, lane, gave_up);
+      if (lane == 0) {
+        s_excl[i & 1] = e;
+        if (tile == tiles - 1 && red.ops && !gave_up)
+          finish_reduction<Op, C>(red, hdr, Op::cadd(e, agg), (uint32_t)tiles, timeout_ns);
+      }
+      __syncwarp();
+      bar_arrive_n(kBarExcl + (i & 1), kBlockThreads);
+    }
+    return;
+  }
+
+  // ---- the compute warps
+  const auto f = kernel_map<F>(P);
+  const bool minmax = (red.ops & (TR_MIN | TR_MAX)) != 0;
+  const Carry carry = carry_in ? Carry(*carry_in) : Carry(0);
+  C* const rows0 = reinterpret_cast<C*>(s_dyn);
+  uint4 raw[kLoads];
+  auto full_tile = [&](int64_t t) { return vec_ok && t * kTile + kTile <= n; };
+  auto fetch = [&](int64_t t) {  // a full tile's vectors into registers (loads in flight)
+    const uint4* xv = reinterpret_cast<const uint4*>(x + t * kTile);
+#pragma unroll
+    for (int j = 0; j < kLoads; ++j) raw[j] = ld_stream(xv + j * kThreads + tid);
+  };
+  // tile t's outputs from its scanned-in-place row buffer, given its exclusive prefix
+  auto write_out = [&](int64_t t, C* rows, Carry excl, const T& thread_off) {
+    const int64_t t0 = t * kTile;
+    const bool full = full_tile(t);
+    C* row = rows + tid * kRow;
+    const Carry prefix = Op::cadd(carry, excl);
+    T run;
+    if constexpr (std::is_same<Op, OpF32>::value) {
+      run = ff_add(ff_from_double(prefix), thread_off);
+    } else {
+      run = Op::add((T)prefix, thread_off);
+    }
+    if constexpr (sizeof(Out) == 4) {
+      Out* orow = reinterpret_cast<Out*>(row);
+      if (exclusive) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+          const Out o = run_out<Op>(run);
+          run_add<Op>(run, row[i]);
+          orow[i] = o;  // in place: this thread alone reads and writes its row
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+          run_add<Op>(run, row[i]);
+          orow[i] = run_out<Op>(run);
+        }
+      }
+      compute_sync();
+      const Out* orows = reinterpret_cast<const Out*>(rows);
+      if (full) {
+        uint4* yv = reinterpret_cast<uint4*>(y + t0);
+#pragma unroll
+        for (int j = 0; j < kTile / 4 / kThreads; ++j) {
+          const int p0 = (j * kThreads + tid) * 4;
+          Out o[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) o[q] = orows[((p0 + q) / kItems) * kRow + (p0 + q) % kItems];
+          st_stream(yv + j * kThreads + tid, pack16(o));
+        }
+      } else {
+        for (int p = tid; p < kTile && t0 + p < n; p += kThreads) y[t0 + p] = orows[(p / kItems) * kRow + p % kItems];
+      }
+    } else {
+      const int64_t base = t0 + (int64_t)tid * kItems;
+      constexpr int kPer = 16 / (int)sizeof(Out);
+#pragma unroll
+      for (int g = 0; g < kItems / kPer; ++g) {
+        Out o[kPer];
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+          if (exclusive) {
+            o[q] = run_out<Op>(run);
+            run_add<Op>(run, row[g * kPer + q]);
+          } else {
+            run_add<Op>(run, row[g * kPer + q]);
+            o[q] = run_out<Op>(run);
+          }
+        }
+        if (full) {
+          st_stream(reinterpret_cast<uint4*>(y + base) + g, pack16(o));
+        } else {
+#pragma unroll
+          for (int q = 0; q < kPer; ++q)
+            if (base + g * kPer + q < n) y[base + g * kPer + q] = o[q];
+        }
+      }
+    }
+    compute_sync();  // the buffer is free for the tile after next
+  };
+
+  if (tid == 0) s_next = atomicAdd(&hdr->tile_counter, 1u);
+  compute_sync();
+  int64_t t = s_next;
+  if (t < tiles && full_tile(t)) fetch(t);
+  int64_t t_prev = -1;
+  T prev_off = Op::zero();  // tile t_prev: this thread's offset within it (warp offset + lane offset)
+  int i = 0;
+  while (t < tiles) {
+    compute_sync();  // everyone has read s_next
+    if (tid == 0) s_next = atomicAdd(&hdr->tile_counter, 1u);  // the next tile's id, one ahead
+    C* rows = rows0 + (i & 1) * (kThreads * kRow);
+    const int64_t t0 = t * kTile;
+    const bool full = full_tile(t);
+    if (full) {
+#pragma unroll
+      for (int j = 0; j < kLoads; ++j) {
+        C e[V];
+        S::unpack(raw[j], e);
+        map_vec<V>(f, e);
+        const int p0 = (j * kThreads + tid) * V;
+#pragma unroll
+        for (int q = 0; q < V; ++q) rows[((p0 + q) / kItems) * kRow + (p0 + q) % kItems] = e[q];
+      }
+    } else {
+      for (int p = tid; p < kTile; p += kThreads)
+        rows[(p / kItems) * kRow + p % kItems] = (t0 + p < n) ? f(S::cvt(x[t0 + p])) : C(0);
+    }
+    compute_sync();
+    C* row = rows + tid * kRow;
+    T acc = Op::zero();
+#pragma unroll
+    for (int k = 0; k < kItems; ++k) run_add<Op>(acc, row[k]);
+    if (minmax) {  // the tile's min / max of f over its valid elements, combined per warp
+      C mn = mm_highest<C>(), mx = mm_lowest<C>();
+      const int64_t valid = full ? kItems : imax<int64_t>(0, imin<int64_t>(kItems, n - t0 - (int64_t)tid * kItems));
+#pragma unroll
+      for (int k = 0; k < kItems; ++k) {
+        if (k < valid) {
+          mn = mm_min(mn, row[k]);
+          mx = mm_max(mx, row[k]);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = mm_min(mn, __shfl_xor_sync(kFull, mn, o));
+        mx = mm_max(mx, __shfl_xor_sync(kFull, mx, o));
+      }
+      if (lane == 0) {
+        s_mn[tid >> 5] = mn;
+        s_mx[tid >> 5] = mx;
+      }
+    }
+    T warp_off, excl_lane, tile_tot;
+    block_totals<Op>(acc, s_warp, warp_off, excl_lane, tile_tot);  // (its barrier also publishes s_mn / s_mx, s_next)
+    if (tid == 0) {
+      if (minmax) {
+        // fold the tile's min / max into the header words without waiting, then count the tile
+        // (release: the folds are visible to whoever sees the count)
+        C mn = s_mn[0], mx = s_mx[0];
+#pragma unroll
+        for (int w = 1; w < kWarps; ++w) {
+          mn = mm_min(mn, s_mn[w]);
+          mx = mm_max(mx, s_mx[w]);
+        }
+        if (mn == mn) red_max_u32(&hdr->red_min, ~mm_key(mn));  // NaN (only NaN values) adds nothing
+        if (mx == mx) red_max_u32(&hdr->red_max, mm_key(mx));
+        red_add_release_u32(&hdr->red_done, 1u);
+      }
+      s_agg[i & 1] = Op::to_carry(tile_tot);
+      s_tile_of[i & 1] = t;
+    }
+    bar_arrive_n(kBarAgg + (i & 1), kBlockThreads);  // tile t goes to the look-back warp
+    const int64_t t_next = s_next;
+    if (t_next < tiles && full_tile(t_next)) fetch(t_next);  // in flight during the outputs below
+    if (t_prev >= 0) {
+      bar_sync_n(kBarExcl + ((i - 1) & 1), kBlockThreads);
+      write_out(t_prev, rows0 + ((i - 1) & 1) * (kThreads * kRow), s_excl[(i - 1) & 1], prev_off);
+    }
+    t_prev = t;
+    prev_off = Op::add(warp_off, excl_lane);
+    t = t_next;
+    ++i;
+  }
+  if (t_prev >= 0) {
+    bar_sync_n(kBarExcl + ((i - 1) & 1), kBlockThreads);
+    write_out(t_prev, rows0 + ((i - 1) & 1) * (kThreads * kRow), s_excl[(i - 1) & 1], prev_off);
+  }
+  if (tid == 0) s_tile_of[i & 1] = -1;
+  bar_arrive_n(kBarAgg + (i & 1), kBlockThreads);  // the look-back warp stops
+}
+
+// Clear the scan state and launch k_scan for the storage type In, map F and
+// output arithmetic Op; P is the map's source.
+template <class In, class F, class Op, class Src>
+tr_status launch(const Src& P, const In* x, typename Op::Out* y, int64_t n, const typename Op::Out* carry,
+                 const tr_exec* e, const ScanOpts& opt) {
+  const int64_t tiles = std::max<int64_t>(1, ceil_div(n, kTile));  // n = 0 (with a reduction): one empty tile
+  if (tiles > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "too many tiles");
+  const ScanWs ws{reinterpret_cast<unsigned char*>(ws_body(e))};
+  const uint64_t timeout_ns = (uint64_t)(e->wait_timeout_us ? e->wait_timeout_us : 1000000u) * 1000ull;
+  const int vec_ok = aligned_to(x, 16) && aligned_to(y, 16);
+  cudaStream_t st = stream_of(e);
+  WsHeader* hdr = ws_header(e);
+  const ScanRed red{opt.sum, opt.mn, opt.mx, (int32_t)opt.sum_t, opt.ops};
+  // every call starts from a zero tile counter, cleared reduction words and clear look-back
+  // lines: one memset from the counter through the last line (the error words before the
+  // counter are left alone)
+  unsigned char* from = reinterpret_cast<unsigned char*>(&hdr->tile_counter);
+  const size_t bytes = (size_t)(reinterpret_cast<unsigned char*>(ws.lines) - from) + (size_t)tiles * kLineBytes;
+  tr_status s = cuda_status(cudaMemsetAsync(from, 0, bytes, st), "cudaMemsetAsync(scan state)");
+  if (s) return s;
+  auto kern = k_scan<In, F, Op, Src>;
+  if ((s = ensure_dyn_smem((const void*)kern, (int)kDynBytes, "cudaFuncSetAttribute(k_scan)"))) return s;
+  // persistent: at most the resident blocks (every block that holds a tile id runs)
+  const int64_t resident = (int64_t)dev_info().sm_count * blocks_per_sm((const void*)kern, kBlockThreads, kDynBytes);
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, resident));
+  kern<<<(unsigned)grid, kBlockThreads, kDynBytes, st>>>(x, y, n, vec_ok, P, hdr, ws, carry, timeout_ns,
+                                                         e->debug_stall_tile, opt.exclusive, red, tiles);
+  return launch_status("k_scan");
+}
+
+}  // namespace scank
+}  // namespace tr

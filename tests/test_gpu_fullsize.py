@@ -1,16 +1,21 @@
 """Parity at the benchmark's full sizes, in the launch configurations the
-benchmark times, against the oracle on outputs it can afford:
+benchmark times, against the oracle (run on all host cores):
 
   * segmented rational 6/6, 2^28 elements, 65,536 segments (the headline):
-    256 segments spread over the array (every launch-range boundary class is
-    hit at this density), each against the oracle on its own slice;
-  * u32 splitmix32 scan mod 2^32, 2^28: every output, bit for bit (the
-    oracle's integer scan runs in a few seconds);
+    every segment's sum within the stated bar of 1e-6 normwise
+    (|s - s_ref| / sum |f_ref|), min and max within 1e-5 of max |f_ref|;
+  * u32 splitmix32 scan mod 2^32, 2^28: every output, bit for bit;
   * f32 compensated scan of x^2, 2^28: 4,096 sampled prefixes, each exact in
-    the oracle and rounded once, within the given 1e-5 relative bar;
-  * batched, 10,000 arrays: 200 sampled arrays against the oracle;
-  * FP16 storage, Horner 8, 2^30: the whole sum, min and max (the oracle's
-    exact sum over 2^26-element chunks, combined in FP64).
+    the oracle and rounded once, within the stated 1e-5 relative bar;
+  * batched, 10,000 arrays: every array's compensated sum within 1e-6
+    normwise of the exact sum of its binary32 map values (bit-identical to the
+    device's), min and max equal to theirs; the error against FP64 evaluation,
+    which includes the FP32 map's own rounding (up to ~2e-5 for degree-16
+    Horner at |x| near 2), is printed;
+  * FP16 storage, Horner 8, 2^30: the whole sum within 1e-6 normwise, min and
+    max within 1e-5 of max |f_ref|.
+The per-element error bounds derived from the FP32 arithmetic (tests/helpers)
+are printed beside the achieved errors as a diagnostic.
 Inputs come from the same seeded generators as the benchmark."""
 import numpy as np
 import pytest
@@ -33,7 +38,13 @@ def B():
     return binding
 
 
-def test_headline_segmented_sampled_segments(orc, B):
+def _minmax_err(lo, hi, rlo, rhi):
+    lo, hi, rlo, rhi = (np.atleast_1d(np.asarray(v, dtype=np.float64)) for v in (lo, hi, rlo, rhi))
+    scale = np.maximum(np.maximum(np.abs(rlo), np.abs(rhi)), 1e-300)
+    return float(np.max(np.maximum(np.abs(lo - rlo), np.abs(hi - rhi)) / scale))
+
+
+def test_headline_segmented_all_segments(orc, B):
     x, m, off = I.rational_segments(1 << 28, 65536)
     n, nseg = x.size, off.size - 1
     xd = torch.from_numpy(x).cuda()
@@ -45,20 +56,21 @@ def test_headline_segmented_sampled_segments(orc, B):
     ex = B.make_exec(ws)
     B.tr_segmented_reduce(m, xd, offd, B.TR_SUM | B.TR_MIN | B.TR_MAX, sums, mins, maxs, ex)
     B.tr_check(ex)
-    s, lo, hi = sums.cpu().numpy(), mins.cpu().numpy().astype(np.float64), maxs.cpu().numpy().astype(np.float64)
+    s, lo, hi = sums.cpu().numpy(), mins.cpu().numpy(), maxs.cpu().numpy()
     del xd
     spec = oracle_map(orc, m)
-    pick = np.unique(np.concatenate([np.linspace(0, nseg - 1, 250).astype(np.int64), [0, 1, nseg - 2, nseg - 1]]))
-    for k in pick:
-        a, b = int(off[k]), int(off[k + 1])
-        xs = x[a:b].astype(np.float64)
-        rs, rlo, rhi = orc.reduce_float(spec, xs)
-        f = orc.map_values(spec, xs)
-        bnd = map_error_bound(m, xs, f)
-        tol = 1e-6 * np.sum(np.abs(f)) + np.sum(bnd) + 1e-30
-        assert abs(s[k] - rs) <= tol, (k, s[k], rs, tol)
-        mb = np.max(bnd) + 2.0 ** -24 * max(abs(rlo), abs(rhi))
-        assert abs(lo[k] - rlo) <= mb and abs(hi[k] - rhi) <= mb, k
+    rs, rlo, rhi, ra = orc.segmented_reduce_float_mt(spec, x, off)
+    err = np.abs(s - rs) / ra
+    assert err.max() <= 1e-6, (int(np.argmax(err)), err.max())
+    emm = _minmax_err(lo, hi, rlo, rhi)
+    assert emm <= 1e-5, emm
+    # diagnostic: the derived per-element bound summed over the worst segment
+    k = int(np.argmax(err))
+    a, b = int(off[k]), int(off[k + 1])
+    xs = x[a:b].astype(np.float64)
+    bound = np.sum(map_error_bound(m, xs, orc.map_values(spec, xs))) / ra[k]
+    print(f"headline: max normwise sum error {err.max():.3g} (segment {k}; derived bound there {bound:.3g}), "
+          f"min/max {emm:.3g}")
 
 
 def test_u32_scan_full_size_bitexact(orc, B):
@@ -91,7 +103,7 @@ def test_f32_scan_full_size_sampled_prefixes(orc, B):
     assert np.all(np.abs(got - ref) <= 1e-5 * np.abs(ref) + 1e-30), np.max(np.abs(got - ref) / np.abs(ref))
 
 
-def test_batched_full_config_sampled_arrays(orc, B):
+def test_batched_full_config_all_arrays(orc, B):
     xs, lens, maps = I.batched(10000)
     dev = [torch.from_numpy(a).cuda() for a in xs]
     n = len(xs)
@@ -104,15 +116,22 @@ def test_batched_full_config_sampled_arrays(orc, B):
     s, lo, hi = sums.cpu().numpy(), mins.cpu().numpy(), maxs.cpu().numpy()
     plan.close()
     del dev
-    for a in np.random.default_rng(9).choice(n, 200, replace=False):
-        xd64 = xs[a].astype(np.float64)
+    es, e64, em64 = np.zeros(n), np.zeros(n), np.zeros(n)
+    for a in range(n):
         spec = oracle_map(orc, maps[a])
-        rs, rlo, rhi = orc.reduce_float(spec, xd64)
-        f = orc.map_values(spec, xd64)
-        bnd = map_error_bound(maps[a], xd64, f)
-        assert abs(s[a] - rs) <= 1e-6 * np.sum(np.abs(f)) + np.sum(bnd) + 1e-30, (a, s[a], rs)
-        mb = np.max(bnd) + 2.0 ** -24 * max(abs(rlo), abs(rhi))
-        assert abs(lo[a] - rlo) <= mb and abs(hi[a] - rhi) <= mb, a
+        th = None if xs[a].size >= 65536 else 1
+        # the FP32 map values (bit-identical on the device): compensated sums within 1e-6 normwise,
+        # min / max exact
+        rs, rlo, rhi, ra = orc.reduce_float_mt(spec, xs[a], th, f32=True)
+        es[a] = abs(s[a] - rs) / max(ra, 1e-300)
+        assert lo[a] == rlo and hi[a] == rhi, a
+        # against FP64 evaluation: the FP32 map's own error included (reported)
+        rs, rlo, rhi, ra = orc.reduce_float_mt(spec, xs[a], th)
+        e64[a] = abs(s[a] - rs) / max(ra, 1e-300)
+        em64[a] = _minmax_err(lo[a], hi[a], rlo, rhi)
+    assert es.max() <= 1e-6, (int(np.argmax(es)), es.max())
+    print(f"batched: max normwise sum error {es.max():.3g} against the binary32 map values, "
+          f"{e64.max():.3g} against FP64 evaluation (min/max {em64.max():.3g}) over {n} arrays")
 
 
 def test_f16_storage_full_size(orc, B):
@@ -126,19 +145,9 @@ def test_f16_storage_full_size(orc, B):
     B.tr_check(ex)
     s, lo, hi = float(out[0]), float(mm[0]), float(mm[1])
     del xd
-    spec = oracle_map(orc, m)
-    total, sabs, bsum, rlo, rhi, bmax = 0.0, 0.0, 0.0, np.inf, -np.inf, 0.0
-    step = 1 << 26
-    for a in range(0, x.size, step):
-        xc = x[a:a + step].astype(np.float64)
-        rs, clo, chi = orc.reduce_float(spec, xc)
-        f = orc.map_values(spec, xc)
-        bnd = map_error_bound(m, xc, f)
-        total += rs
-        sabs += float(np.sum(np.abs(f)))
-        bsum += float(np.sum(bnd))
-        bmax = max(bmax, float(np.max(bnd)))
-        rlo, rhi = min(rlo, clo), max(rhi, chi)
-    assert abs(s - total) <= 1e-6 * sabs + bsum, (s, total)
-    mb = bmax + 2.0 ** -24 * max(abs(rlo), abs(rhi))
-    assert abs(lo - rlo) <= mb and abs(hi - rhi) <= mb
+    rs, rlo, rhi, ra = orc.reduce_float_mt(oracle_map(orc, m), x)
+    err = abs(s - rs) / ra
+    emm = _minmax_err(lo, hi, rlo, rhi)
+    assert err <= 1e-6, err
+    assert emm <= 1e-5, emm
+    print(f"f16 storage: normwise sum error {err:.3g}, min/max {emm:.3g}")

@@ -80,6 +80,8 @@ def test_map_float(orc, B, mi, dt, n, off):
     ref = orc.map_values(oracle_map(orc, m), xh)
     got = y.cpu().double().numpy()
     assert np.all(np.abs(got - ref) <= map_error_bound(m, xh, ref)), np.max(np.abs(got - ref))
+    # the same sequence in binary32: bit for bit
+    assert np.array_equal(got.view(np.int64), orc.map_values_f32(oracle_map(orc, m), xh).view(np.int64))
 
 
 @pytest.mark.parametrize("mi", range(len(MAPS)), ids=MAP_IDS)
@@ -155,6 +157,10 @@ def check_float_reduce(orc, m, xh, got, sum_f32=False):
     if xh.size:
         mb = np.max(bnd) + 2.0 ** -24 * max(abs(lo_ref), abs(hi_ref))
         assert abs(lo - lo_ref) <= mb and abs(hi - hi_ref) <= mb
+        # against the binary32 map values: the compensated sum within 1e-6 normwise, min / max exact
+        s32, lo32, hi32, a32 = orc.reduce_float_mt(oracle_map(orc, m), xh, 1, f32=True)
+        assert abs(s - s32) <= 1e-6 * a32 + (abs(s32) * 2.0 ** -24 if sum_f32 else 0.0), (s, s32, a32)
+        assert lo == lo32 and hi == hi32
     else:
         assert s == 0.0 and lo == np.inf and hi == -np.inf
 
@@ -357,6 +363,10 @@ def check_seg(orc, m, xh, off, got):
     mb = b.max() if b.size else 0.0
     assert np.all(np.abs(lo[ne] - rlo[ne]) <= mb + 2.0 ** -24 * np.abs(rlo[ne]))
     assert np.all(np.abs(hi[ne] - rhi[ne]) <= mb + 2.0 ** -24 * np.abs(rhi[ne]))
+    # against the binary32 map values: compensated sums within 1e-6 normwise, min / max exact
+    s32, lo32, hi32, a32 = orc.segmented_reduce_float_mt(oracle_map(orc, m), xh, off, f32=True)
+    assert np.all(np.abs(s - s32) <= 1e-6 * a32), np.max(np.abs(s - s32) / np.maximum(a32, 1e-300))
+    assert np.array_equal(lo[ne], lo32[ne]) and np.array_equal(hi[ne], hi32[ne])
 
 
 def offsets_random(n, nseg, seed, max_len=8192):

@@ -443,3 +443,89 @@ def test_exclusive_scans(orc):
     m = orc.MapSpec("rational", [1.0, -2.0, 0.5], [1.0, 0.0, 0.3])
     inc, exc = orc.scan_float(m, xf, 24), orc.scan_float(m, xf, 24, exclusive=True)
     assert exc[0] == 0.0 and np.array_equal(exc[1:], inc[:-1])
+
+
+# --------------------------------------------------------------------------
+# binary32 evaluation of the maps
+# --------------------------------------------------------------------------
+
+def _rn32(fr: Fraction) -> float:
+    """Round a rational to the nearest binary32 value, ties to even (subnormals included)."""
+    if fr == 0:
+        return 0.0
+    sign = -1.0 if fr < 0 else 1.0
+    a = abs(fr)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    q = max(e - 23, -149)
+    m = a / Fraction(2) ** q
+    n = m.numerator // m.denominator
+    r = m - n
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    return sign * float(n) * 2.0 ** q
+
+
+def _f32_values(g, k, scale=1.0):
+    return (g.standard_normal(k) * scale).astype(np.float32).astype(np.float64)
+
+
+def test_map_f32_bruteforce(orc):
+    """Every binary32 map equals its operation sequence carried out with exact
+    rationals and one round-to-nearest-even to binary32 per operation."""
+    g = np.random.default_rng(32)
+    x = np.concatenate([_f32_values(g, 60, 2.0), [0.0, -0.0, 1.0, -3.0, 1e-30]])
+    cp = _f32_values(g, 9)
+    cq = (np.abs(_f32_values(g, 5)) + 0.5).astype(np.float32).astype(np.float64)
+    horner = orc.MapSpec("horner", cp)
+    rational = orc.MapSpec("rational", cp[:7], cq)
+    newton = orc.MapSpec("newton_cbrt", iters=6)
+
+    def horner_rn(c, v):
+        p = Fraction(c[-1])
+        for ck in c[-2::-1]:
+            p = Fraction(_rn32(p * Fraction(v) + Fraction(ck)))
+        return p
+
+    got_h = orc.map_values_f32(horner, x)
+    got_r = orc.map_values_f32(rational, x)
+    got_n = orc.map_values_f32(newton, x)
+    for i, v in enumerate(x):
+        assert got_h[i] == float(horner_rn(cp, v))
+        assert got_r[i] == _rn32(horner_rn(cp[:7], v) / horner_rn(cq, v))
+        y = Fraction(-1 if math.copysign(1.0, v) < 0 else 1)
+        for _ in range(6):
+            yy = Fraction(_rn32(y * y))
+            q = Fraction(_rn32(Fraction(v) / yy))
+            s = Fraction(_rn32(2 * y + q))
+            y = Fraction(_rn32(s / 3))
+        assert got_n[i] == float(y), (v, got_n[i], float(y))
+
+
+def test_map_f32_matches_numpy_binary32(orc):
+    """x^2 and P/Q with degree-0 polynomials are single binary32 operations:
+    numpy's float32 arithmetic gives them independently."""
+    g = np.random.default_rng(33)
+    x = g.standard_normal(10_000).astype(np.float32)
+    assert np.array_equal(orc.map_values_f32(orc.MapSpec("square"), x), (x * x).astype(np.float64))
+    a, b = np.float32(1.7), g.uniform(0.5, 4.0, 10_000).astype(np.float32)
+    got = np.array([orc.map_values_f32(orc.MapSpec("rational", [float(a)], [float(bb)]), [0.0])[0] for bb in b[:500]])
+    assert np.array_equal(got, (a / b[:500]).astype(np.float64))
+
+
+def test_reduce_mt_f32_values(orc):
+    """With f32=True the threaded reductions sum the binary32 map values exactly."""
+    g = np.random.default_rng(34)
+    x = g.uniform(-2, 2, 20_001).astype(np.float32)
+    m = orc.MapSpec("horner", _f32_values(g, 13))
+    f = orc.map_values_f32(m, x)
+    s, lo, hi, sa = orc.reduce_float_mt(m, x, 3, f32=True)
+    assert s == math.fsum(f) and lo == f.min() and hi == f.max() and sa == math.fsum(np.abs(f))
+    off = np.array([0, 5, 5, 9000, 20_001], dtype=np.int64)
+    ss, sl, sh, sa = orc.segmented_reduce_float_mt(m, x, off, 2, f32=True)
+    for k in range(4):
+        seg = f[off[k]:off[k + 1]]
+        assert ss[k] == math.fsum(seg) and sa[k] == math.fsum(np.abs(seg))
+        if seg.size:
+            assert sl[k] == seg.min() and sh[k] == seg.max()
