@@ -127,14 +127,19 @@ uint64_t tr_launch_count(void);
 tr_status tr_workspace_init(void* d_workspace, size_t bytes, void* stream);
 
 /* Synchronise exec->stream, then read and clear the device status word in
- * exec->workspace.  Returns TR_ERR_CUDA if the stream reported an error,
+ * exec->workspace -- the host side of the paper's error convention (Sec. 1.2.1
+ * "Cuda error checking") for errors a kernel found (Sec. 2.4's release_assert
+ * reports instead of trapping here).  Returns TR_ERR_CUDA if the stream reported an error,
  * otherwise the first device-side error recorded since the last tr_check
  * (TR_ERR_TIMEOUT, TR_ERR_DEVICE_ASSERT) or TR_OK. */
 tr_status tr_check(const tr_exec* exec);
 
 /* ---- map ------------------------------------------------------------------ */
 
-/* y_i = f(x_i), i < n.  xt: F16/BF16/F32 (FP32 compute), F64 (FP64 compute) or
+/* y_i = f(x_i), i < n: the map family of tr_map_kind, written once as hdc
+ * functions (the paper's Sec. 2.3 "host device everything" and Sec. 2.6) and
+ * evaluated on the device with the same operation sequence as on the host.
+ * xt: F16/BF16/F32 (FP32 compute), F64 (FP64 compute) or
  * U32 (mixers and identity).  yt is the compute type: F32 for FP32 compute,
  * F64 for F64, U32 for U32.  y may equal x when xt == yt; partial overlap is
  * an error.  Needs no workspace (exec->workspace may be NULL).  Pointers must
@@ -147,7 +152,10 @@ tr_status tr_map(const tr_map_desc* map, const void* d_x, tr_dtype xt, void* d_y
 
 tr_status tr_reduce_workspace_size(int64_t n, tr_dtype xt, size_t* bytes);
 
-/* sum / min / max of f(x_i), i < n, selected by ops (TR_SUM|TR_MIN|TR_MAX).
+/* sum / min / max of f(x_i), i < n, selected by ops (TR_SUM|TR_MIN|TR_MAX) -- the
+ * plain transform-reduce (e.g. 2^20 FP64 values through a degree-8 Horner
+ * polynomial, or 2^30 FP16-stored values with FP32 compute); compensated sums
+ * (Kahan 1965) combined with error-free additions (Knuth's TwoSum).
  * Results are written to DEVICE memory (one element each):
  *   FP32 compute: per-thread compensated (Kahan) sums of pairwise vector sums,
  *                 float-float warp/block combination, FP64 across blocks;
@@ -163,7 +171,9 @@ tr_status tr_reduce(const tr_map_desc* map, const void* d_x, tr_dtype xt, int64_
 
 tr_status tr_segmented_reduce_workspace_size(int64_t n, int64_t n_seg, tr_dtype xt, size_t* bytes);
 
-/* For each segment s < n_seg, elements [d_offsets[s], d_offsets[s+1]) of x:
+/* The segmented transform-reduce (e.g. 2^28 FP32 values through a rational
+ * map of degree 6/6 into 65,536 segments).
+ * For each segment s < n_seg, elements [d_offsets[s], d_offsets[s+1]) of x:
  * sum / min / max of f into d_sums[s], d_mins[s], d_maxs[s] (device arrays).
  * d_offsets: n_seg + 1 int64 device values, offsets[0] = 0,
  * offsets[n_seg] = n, non-decreasing; empty segments get the identities.
@@ -194,7 +204,9 @@ tr_status tr_segmented_reduce_host(const tr_map_desc* map, const void* h_x, tr_d
 
 tr_status tr_scan_workspace_size(int64_t n, tr_dtype xt, tr_dtype yt, size_t* bytes);
 
-/* y_i = f(x_0) + ... + f(x_i), single pass with decoupled look-back between
+/* The inclusive scan of f (e.g. 2^28 u32 through splitmix32 modulo 2^32, or
+ * 2^28 f32 of x^2 with compensated sums):
+ * y_i = f(x_0) + ... + f(x_i), single pass with decoupled look-back between
  * tiles (Merrill & Garland, "Single-pass parallel prefix scan with decoupled
  * look-back", NVIDIA NVR-2016-002).  Supported (xt -> yt):
  *   U32 -> U32  modulo 2^32 (bit exact)
@@ -236,23 +248,29 @@ tr_status tr_scan_reduce(const tr_map_desc* map, const void* d_x, tr_dtype xt, v
 
 typedef struct tr_batch_plan tr_batch_plan; /* opaque, owned by the library */
 
-/* Plan the reduction of n_arrays independent f32 device arrays, each with its
- * own map (FP32 compute; Horner, rational, Newton cube root, square,
- * identity), in ONE persistent kernel launch replayed from a CUDA graph.
- *   d_xs[i]   (host array of device pointers) array i, lens[i] elements
+/* Plan the reduction of n_arrays independent device arrays of storage type xt
+ * (F32, F16 or BF16; FP32 compute), each with its own map (Horner, rational,
+ * Newton cube root, square, identity), in ONE persistent kernel launch
+ * replayed from a CUDA graph -- the batched workload (e.g. 10,000 arrays with
+ * lengths log-uniform in [1, 2^20] and mixed maps), with an autotuned launch
+ * shape.
+ *   d_xs[i]   (host array of device pointers) array i, lens[i] elements,
+ *             aligned to the element size
  *   maps[i]   its map (host descriptors, copied)
  *   d_sums / d_mins / d_maxs  device arrays of n_arrays F64 / F32 / F32
  *             (those selected by ops must be non-NULL)
  * Each array is cut into work items; warps pull items from an atomic queue
- * (longest first), reduce them with compensated FP32 sums, and the warp that
+ * (costliest first), reduce them with compensated FP32 sums, and the warp that
  * finishes an array's last item joins its partials in FP64 in item order, so
- * results are bitwise deterministic.  autotune != 0 times tile and block-size
- * candidates on this data (it writes the outputs and synchronises the device;
- * TR_AUTOTUNE_CACHE names an optional cache file); 0 takes a fixed default.
- * Plan creation allocates the plan's device buffers and instantiates the
- * graph; the arrays and outputs must stay valid while the plan is used. */
+ * results are bitwise deterministic.  autotune != 0 times the launch shapes
+ * -- item size T in {8K, 16K, 32K, 64K}, 128 or 256 threads, items equal in
+ * elements or balanced by map cost -- on this data (it writes the outputs and
+ * synchronises the device; TR_AUTOTUNE_CACHE names an optional cache file);
+ * 0 takes a fixed default.  Plan creation allocates the plan's device buffers
+ * and instantiates the graph; the arrays and outputs must stay valid while
+ * the plan is used. */
 tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, const int64_t* lens,
-                                 const tr_map_desc* maps, unsigned ops, double* d_sums, float* d_mins,
+                                 const tr_map_desc* maps, tr_dtype xt, unsigned ops, double* d_sums, float* d_mins,
                                  float* d_maxs, int autotune, void* stream, tr_batch_plan** out);
 
 /* Launch the plan's graph on stream (one cudaGraphLaunch).  Runs of one plan
@@ -277,10 +295,10 @@ enum { TR_PREC_BF16X3 = 0, TR_PREC_FP32 = 1, TR_PREC_BF16X6 = 2 };
  * per-column partial results of the tensor path. */
 tr_status tr_vandermonde_workspace_size(int64_t m, int64_t npoly, size_t* bytes);
 
-/* Many polynomials at many points (the dense workload of the brief: 4096
- * polynomials of degree 31 at 2^20 points, "Vandermonde GEMM on tcgen05/TMEM"
- * with split-BF16): Y = V(x) C, Y[i][j] = sum_k C[k][j] x_i^k, written out
- * and/or reduced per column (polynomial j) over the points.
+/* Many polynomials at many points (the dense workload, e.g. 4096 polynomials
+ * of degree 31 at 2^20 points), as a Vandermonde product on the tensor cores:
+ * Y = V(x) C, Y[i][j] = sum_k C[k][j] x_i^k, written out and/or reduced per
+ * column (polynomial j) over the points.
  *   d_x     m FP32 points;  d_coef (deg+1) x npoly FP32, row-major, row k
  *           holding the power-k coefficients of all polynomials (deg <= 31);
  *   d_y     m x npoly row-major in yt: TR_F32, TR_BF16 (rounded to nearest

@@ -75,7 +75,7 @@ SIGNATURES = {
     "tr_scan": ([_M, _P, _I32, _P, _I32, _I64, _P, _E], _I32),
     "tr_scan_noalloc": ([_M, _P, _I32, _P, _I32, _I64, _P, _P, _P], _I32),
     "tr_scan_reduce": ([_M, _P, _I32, _P, _I32, _I64, _I32, _P, _U32, _P, _I32, _P, _P, _E], _I32),
-    "tr_batched_plan_create": ([_I64, _P, _P, _M, _U32, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)], _I32),
+    "tr_batched_plan_create": ([_I64, _P, _P, _M, _I32, _U32, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)], _I32),
     "tr_batched_run": ([_P, _P], _I32),
     "tr_batched_run_unbatched": ([_P, _I32, _P], _I32),
     "tr_batched_plan_describe": ([_P], ctypes.c_char_p),
@@ -234,7 +234,7 @@ def tr_scan_noalloc(m: dict, x: torch.Tensor, y: torch.Tensor, status: torch.Ten
 
 
 class BatchPlan:
-    """A tr_batched plan over a list of f32 device tensors, one map dict each."""
+    """A tr_batched plan over a list of device tensors (one storage dtype: f32, f16 or bf16), one map dict each."""
 
     def __init__(self, xs, maps, sums, mins, maxs, ops: int = TR_SUM | TR_MIN | TR_MAX, autotune: bool = False,
                  stream=None):
@@ -243,10 +243,11 @@ class BatchPlan:
         descs = (tr_map_desc * n)(*[d.c for d in self._keep])
         ptrs = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
         lens = (ctypes.c_int64 * n)(*[x.numel() for x in xs])
+        xt = dtype_of(xs[0]) if n else TR_F32
         self._refs = (xs, sums, mins, maxs)
         self.handle = ctypes.c_void_p()
         s = (stream or torch.cuda.current_stream()).cuda_stream
-        _check(lib().tr_batched_plan_create(n, ptrs, lens, descs, ops, _ptr(sums), _ptr(mins), _ptr(maxs),
+        _check(lib().tr_batched_plan_create(n, ptrs, lens, descs, xt, ops, _ptr(sums), _ptr(mins), _ptr(maxs),
                                             int(autotune), s, ctypes.byref(self.handle)))
 
     def describe(self) -> str:

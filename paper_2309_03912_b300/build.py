@@ -31,6 +31,13 @@ FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "
                 "-I" + INCLUDE, "-I" + CSRC]
 
 
+# The shared CUDA runtime: one runtime instance per process (the one torch
+# loads), so that code instantiating the kernel templates of tr.hpp in another
+# library shares kernel registrations, errors and streams with this one.
+CUDA_LIB = os.path.join(os.path.dirname(os.path.dirname(NVCC)), "lib64")
+LINK = ["-cudart", "shared", "-lcuda", "-Xlinker", "-rpath=" + CUDA_LIB]
+
+
 def _headers() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
                   glob.glob(os.path.join(INCLUDE, "*.h")))
@@ -73,7 +80,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     newest = max(os.path.getmtime(o) for o in objs)
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcuda"]
+        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + LINK
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

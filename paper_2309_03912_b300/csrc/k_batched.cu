@@ -39,7 +39,7 @@ namespace tr {
 namespace {
 
 struct BatchArray {
-  const float* x;
+  const void* x;  // storage type of the plan
   int64_t len;
   int32_t kind, deg_p, deg_q, iters;
   int32_t first_slot, n_items;
@@ -111,39 +111,41 @@ struct MakeBatchMap<NewtonCbrt<float, -1>> {
   }
 };
 
-template <class F>
+template <class In, class F>
 __device__ __forceinline__ Acc<float> run_item(const BatchArray& A, const BatchItem& it, int lane) {
   const auto f = Packed<F>::make(MakeBatchMap<F>::make(A));  // coefficient pairs in registers
-  return warp_reduce_range<float>(A.x, it.start, it.start + it.count, A.aligned, f, lane, it.start + it.count);
+  return warp_reduce_range<In>(static_cast<const In*>(A.x), it.start, it.start + it.count, A.aligned, f, lane,
+                               it.start + it.count);
 }
 
+template <class In>
 __device__ __noinline__ Acc<float> dispatch_item(const BatchArray& A, const BatchItem& it, int lane) {
   switch (A.kind) {
     case TR_MAP_HORNER:
       switch (A.deg_p) {
-        case 4: return run_item<Horner<float, 4>>(A, it, lane);
-        case 5: return run_item<Horner<float, 5>>(A, it, lane);
-        case 6: return run_item<Horner<float, 6>>(A, it, lane);
-        case 7: return run_item<Horner<float, 7>>(A, it, lane);
-        case 8: return run_item<Horner<float, 8>>(A, it, lane);
-        case 9: return run_item<Horner<float, 9>>(A, it, lane);
-        case 10: return run_item<Horner<float, 10>>(A, it, lane);
-        case 11: return run_item<Horner<float, 11>>(A, it, lane);
-        case 12: return run_item<Horner<float, 12>>(A, it, lane);
-        case 13: return run_item<Horner<float, 13>>(A, it, lane);
-        case 14: return run_item<Horner<float, 14>>(A, it, lane);
-        case 15: return run_item<Horner<float, 15>>(A, it, lane);
-        case 16: return run_item<Horner<float, 16>>(A, it, lane);
-        default: return run_item<HornerN<float>>(A, it, lane);
+        case 4: return run_item<In, Horner<float, 4>>(A, it, lane);
+        case 5: return run_item<In, Horner<float, 5>>(A, it, lane);
+        case 6: return run_item<In, Horner<float, 6>>(A, it, lane);
+        case 7: return run_item<In, Horner<float, 7>>(A, it, lane);
+        case 8: return run_item<In, Horner<float, 8>>(A, it, lane);
+        case 9: return run_item<In, Horner<float, 9>>(A, it, lane);
+        case 10: return run_item<In, Horner<float, 10>>(A, it, lane);
+        case 11: return run_item<In, Horner<float, 11>>(A, it, lane);
+        case 12: return run_item<In, Horner<float, 12>>(A, it, lane);
+        case 13: return run_item<In, Horner<float, 13>>(A, it, lane);
+        case 14: return run_item<In, Horner<float, 14>>(A, it, lane);
+        case 15: return run_item<In, Horner<float, 15>>(A, it, lane);
+        case 16: return run_item<In, Horner<float, 16>>(A, it, lane);
+        default: return run_item<In, HornerN<float>>(A, it, lane);
       }
     case TR_MAP_RATIONAL:
-      if (A.deg_p == 6 && A.deg_q == 6) return run_item<Rational<float, 6, 6>>(A, it, lane);
-      return run_item<RationalN<float>>(A, it, lane);
+      if (A.deg_p == 6 && A.deg_q == 6) return run_item<In, Rational<float, 6, 6>>(A, it, lane);
+      return run_item<In, RationalN<float>>(A, it, lane);
     case TR_MAP_NEWTON_CBRT:
-      if (A.iters == 6) return run_item<NewtonCbrt<float, 6>>(A, it, lane);
-      return run_item<NewtonCbrt<float, -1>>(A, it, lane);
-    case TR_MAP_SQUARE: return run_item<Square<float>>(A, it, lane);
-    default: return run_item<Identity<float>>(A, it, lane);
+      if (A.iters == 6) return run_item<In, NewtonCbrt<float, 6>>(A, it, lane);
+      return run_item<In, NewtonCbrt<float, -1>>(A, it, lane);
+    case TR_MAP_SQUARE: return run_item<In, Square<float>>(A, it, lane);
+    default: return run_item<In, Identity<float>>(A, it, lane);
   }
 }
 
@@ -153,7 +155,7 @@ __device__ __forceinline__ void store_batch(const BatchOut& o, int64_t a, double
   if ((o.ops & TR_MAX) && o.maxs) o.maxs[a] = mx;
 }
 
-template <int THREADS>
+template <class In, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_batched(const BatchArray* __restrict__ arrays,
                                                      const BatchItem* __restrict__ items, int32_t n_items,
                                                      BatchPartial* partials, uint32_t* counters, uint32_t* queue,
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(THREADS) k_batched(const BatchArray* __restric
     if (i >= n_items) break;
     const BatchItem it = items[i];
     const BatchArray& A = arrays[it.array];
-    const Acc<float>::W w = dispatch_item(A, it, lane).warp();
+    const Acc<float>::W w = dispatch_item<In>(A, it, lane).warp();
     const int32_t n_it = A.n_items;
     if (n_it == 1) {
       if (lane == 0) store_batch(out, it.array, ff_to_double(w.s), w.mn, w.mx);
@@ -202,7 +204,11 @@ __global__ void __launch_bounds__(THREADS) k_batched(const BatchArray* __restric
 typedef void (*BatchedKernel)(const BatchArray*, const BatchItem*, int32_t, BatchPartial*, uint32_t*, uint32_t*,
                               BatchOut);
 
-BatchedKernel kernel_for(int threads) { return threads == 128 ? k_batched<128> : k_batched<256>; }
+BatchedKernel kernel_for(tr_dtype xt, int threads) {
+  if (xt == TR_F16) return threads == 128 ? k_batched<__half, 128> : k_batched<__half, 256>;
+  if (xt == TR_BF16) return threads == 128 ? k_batched<__nv_bfloat16, 128> : k_batched<__nv_bfloat16, 256>;
+  return threads == 128 ? k_batched<float, 128> : k_batched<float, 256>;
+}
 
 // rough per-element instruction cost of a map, for ordering the queue
 double map_cost(const tr_map_desc& m) {
@@ -214,9 +220,13 @@ double map_cost(const tr_map_desc& m) {
   }
 }
 
+// Autotuned launch shape: the work-item size T, the block size, and whether
+// items are balanced by map cost (an array's items then hold about
+// T x cost(Horner 8) / cost(map) elements, so costly maps get shorter items).
 struct Config {
   int64_t tile = 32768;
   int threads = 256;
+  int balance = 0;
 };
 
 }  // namespace
@@ -227,6 +237,7 @@ using namespace tr;
 
 struct tr_batch_plan {
   int64_t n_arrays = 0;
+  tr_dtype xt = TR_F32;
   unsigned ops = 0;
   double* sums = nullptr;
   float* mins = nullptr;
@@ -261,19 +272,25 @@ void free_items(tr_batch_plan* p) {
   p->d_partials = nullptr;
 }
 
-// Build the item list for tile size T and upload it (with the partial slots).
-tr_status build_items(tr_batch_plan* p, int64_t T) {
+// Build the item list for tile size T (balanced by map cost or not) and upload
+// it (with the partial slots).
+tr_status build_items(tr_batch_plan* p, int64_t T, int balance) {
   std::vector<BatchItem> items;
   std::vector<double> cost;
   int32_t slot = 0;
   for (int64_t a = 0; a < p->n_arrays; ++a) {
     const int64_t L = p->lens[a];
-    const int64_t n_it = std::max<int64_t>(1, (L + T - 1) / T);
+    int64_t Ta = T;
+    if (balance) {  // about T x cost(Horner 8) / cost(map), multiples of 256 (vector alignment kept)
+      const double r = 12.0 / map_cost(p->maps[a]);
+      Ta = std::max<int64_t>(1024, std::min<int64_t>(T, ((int64_t)(T * r) / 256) * 256));
+    }
+    const int64_t n_it = std::max<int64_t>(1, (L + Ta - 1) / Ta);
     p->h_arrays[a].first_slot = slot;
     p->h_arrays[a].n_items = (int32_t)n_it;
     const double mc = map_cost(p->maps[a]);
     for (int64_t k = 0; k < n_it; ++k) {
-      const int64_t st = k * T, cnt = std::min<int64_t>(T, L - st);
+      const int64_t st = k * Ta, cnt = std::min<int64_t>(Ta, L - st);
       items.push_back(BatchItem{(int32_t)a, slot + (int32_t)k, st, std::max<int64_t>(cnt, 0)});
       cost.push_back(mc * (double)std::max<int64_t>(cnt, 1) + 200.0);
     }
@@ -303,16 +320,16 @@ tr_status enqueue(tr_batch_plan* p, cudaStream_t st) {
   tr_status s = cuda_status(cudaMemsetAsync(p->d_counters + p->n_arrays, 0, sizeof(uint32_t), st), "memset(queue)");
   if (s) return s;
   const BatchOut out{p->sums, p->mins, p->maxs, p->ops};
-  kernel_for(p->cfg.threads)<<<p->grid, p->cfg.threads, 0, st>>>(p->d_arrays, p->d_items, p->n_items, p->d_partials,
+  kernel_for(p->xt, p->cfg.threads)<<<p->grid, p->cfg.threads, 0, st>>>(p->d_arrays, p->d_items, p->n_items, p->d_partials,
                                                                   p->d_counters, p->d_counters + p->n_arrays, out);
   return launch_status("k_batched");
 }
 
 tr_status set_config(tr_batch_plan* p, const Config& c) {
   p->cfg = c;
-  const BatchedKernel k = kernel_for(c.threads);
+  const BatchedKernel k = kernel_for(p->xt, c.threads);
   p->grid = dev_info().sm_count * blocks_per_sm((const void*)k, c.threads);
-  return build_items(p, c.tile);
+  return build_items(p, c.tile, c.balance);
 }
 
 tr_status time_config(tr_batch_plan* p, cudaStream_t st, float* ms) {
@@ -338,7 +355,8 @@ std::string cache_key(const tr_batch_plan* p) {
   int64_t total = 0;
   for (int64_t L : p->lens) total += L;
   std::ostringstream k;
-  k << prop.name << "|arrays=" << p->n_arrays << "|log2n=" << (int)std::log2((double)std::max<int64_t>(total, 1));
+  k << prop.name << "|xt=" << (int)p->xt << "|arrays=" << p->n_arrays
+    << "|log2n=" << (int)std::log2((double)std::max<int64_t>(total, 1));
   return k.str();
 }
 
@@ -348,11 +366,12 @@ bool cache_lookup(const std::string& key, Config* c) {
   std::ifstream f(path);
   std::string line;
   while (std::getline(f, line)) {
-    const size_t t1 = line.find('\t'), t2 = line.find('\t', t1 + 1);
-    if (t1 == std::string::npos || t2 == std::string::npos) continue;
+    const size_t t1 = line.find('\t'), t2 = line.find('\t', t1 + 1), t3 = line.find('\t', t2 + 1);
+    if (t1 == std::string::npos || t2 == std::string::npos || t3 == std::string::npos) continue;
     if (line.substr(0, t1) == key) {
       c->tile = atoll(line.substr(t1 + 1, t2 - t1 - 1).c_str());
-      c->threads = atoi(line.substr(t2 + 1).c_str());
+      c->threads = atoi(line.substr(t2 + 1, t3 - t2 - 1).c_str());
+      c->balance = atoi(line.substr(t3 + 1).c_str()) != 0;
       return c->tile > 0 && (c->threads == 128 || c->threads == 256);
     }
   }
@@ -363,7 +382,7 @@ void cache_store(const std::string& key, const Config& c) {
   const char* path = getenv("TR_AUTOTUNE_CACHE");
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << '\t' << c.tile << '\t' << c.threads << '\n';
+  f << key << '\t' << c.tile << '\t' << c.threads << '\t' << c.balance << '\n';
 }
 
 tr_status capture(tr_batch_plan* p, bool unbatched, cudaGraphExec_t* out);
@@ -387,10 +406,12 @@ tr_status tr_batched_plan_destroy(tr_batch_plan* p) {
 }
 
 tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, const int64_t* lens,
-                                 const tr_map_desc* maps, unsigned ops, double* d_sums, float* d_mins, float* d_maxs,
-                                 int autotune, void* stream, tr_batch_plan** out) {
+                                 const tr_map_desc* maps, tr_dtype xt, unsigned ops, double* d_sums, float* d_mins,
+                                 float* d_maxs, int autotune, void* stream, tr_batch_plan** out) {
   if (!out) return fail(TR_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
+  if (xt != TR_F32 && xt != TR_F16 && xt != TR_BF16) return fail(TR_ERR_UNSUPPORTED, "batched storage dtype %d", xt);
+  const size_t esz = dtype_size(xt);
   if (n_arrays <= 0 || n_arrays > (int64_t(1) << 30)) return fail(TR_ERR_INVALID_ARG, "n_arrays out of range");
   if (!d_xs || !lens || !maps) return fail(TR_ERR_INVALID_ARG, "arrays, lengths or maps are NULL");
   if (ops == 0 || (ops & ~7u)) return fail(TR_ERR_INVALID_ARG, "ops must be a non-empty mask of TR_SUM|TR_MIN|TR_MAX");
@@ -400,6 +421,7 @@ tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, cons
     return fail(TR_ERR_ALIGNMENT, "outputs misaligned");
   auto* p = new tr_batch_plan();
   p->n_arrays = n_arrays;
+  p->xt = xt;
   p->ops = ops;
   p->sums = d_sums;
   p->mins = d_mins;
@@ -417,13 +439,13 @@ tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, cons
       tr_batched_plan_destroy(p);
       return fail(s, "array %lld: %s", (long long)a, msg.c_str());
     }
-    if (lens[a] < 0 || (lens[a] > 0 && !d_xs[a]) || (d_xs[a] && !aligned_to(d_xs[a], 4))) {
+    if (lens[a] < 0 || (lens[a] > 0 && !d_xs[a]) || (d_xs[a] && !aligned_to(d_xs[a], esz))) {
       tr_batched_plan_destroy(p);
       return fail(TR_ERR_INVALID_ARG, "array %lld: bad pointer or length", (long long)a);
     }
     BatchArray& A = p->h_arrays[a];
     std::memset(&A, 0, sizeof(A));
-    A.x = static_cast<const float*>(d_xs[a]);
+    A.x = d_xs[a];
     A.len = lens[a];
     A.kind = P.kind;
     A.deg_p = P.deg_p;
@@ -458,23 +480,24 @@ tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, cons
   } else if (autotune) {
     float best_ms = 1e30f;
     int tried = 0;
-    for (int64_t T : {8192, 16384, 32768, 65536}) {
-      for (int th : {128, 256}) {
-        Config c;
-        c.tile = T;
-        c.threads = th;
-        float ms = 0.f;
-        if ((s = set_config(p, c)) || (s = time_config(p, st, &ms))) {
-          tr_batched_plan_destroy(p);
-          return s;
+    for (int64_t T : {8192, 16384, 32768, 65536})
+      for (int th : {128, 256})
+        for (int bal : {0, 1}) {
+          Config c;
+          c.tile = T;
+          c.threads = th;
+          c.balance = bal;
+          float ms = 0.f;
+          if ((s = set_config(p, c)) || (s = time_config(p, st, &ms))) {
+            tr_batched_plan_destroy(p);
+            return s;
+          }
+          ++tried;
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+          }
         }
-        ++tried;
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = c;
-        }
-      }
-    }
     cache_store(key, best);
     char b[96];
     snprintf(b, sizeof b, "autotuned over %d candidates (best %.3f ms)", tried, best_ms);
@@ -489,8 +512,8 @@ tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, cons
     return s;
   }
   char b[256];
-  snprintf(b, sizeof b, "tile=%lld threads=%d grid=%d items=%d arrays=%lld (%s)", (long long)best.tile, best.threads,
-           p->grid, p->n_items, (long long)n_arrays, how.c_str());
+  snprintf(b, sizeof b, "tile=%lld threads=%d balance=%d grid=%d items=%d arrays=%lld (%s)", (long long)best.tile,
+           best.threads, best.balance, p->grid, p->n_items, (long long)n_arrays, how.c_str());
   p->desc = b;
   *out = p;
   return TR_OK;
@@ -507,7 +530,7 @@ tr_status tr_batched_run_unbatched(tr_batch_plan* p, int use_graph, void* stream
   if (!p) return fail(TR_ERR_INVALID_ARG, "plan is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!p->d_reduce_ws) {
-    p->reduce_ws_bytes = reduce_ws_bytes(0, TR_F32);
+    p->reduce_ws_bytes = reduce_ws_bytes(0, p->xt);
     tr_status s = cuda_status(cudaMalloc(&p->d_reduce_ws, p->reduce_ws_bytes), "cudaMalloc(reduce workspace)");
     if (!s) s = cuda_status(cudaMemset(p->d_reduce_ws, 0, p->reduce_ws_bytes), "cudaMemset(reduce workspace)");
     if (s) return s;
@@ -523,7 +546,7 @@ tr_status tr_batched_run_unbatched(tr_batch_plan* p, int use_graph, void* stream
   }
   const tr_exec e{stream, p->d_reduce_ws, p->reduce_ws_bytes, 0, 0, -1};
   for (int64_t a = 0; a < p->n_arrays; ++a) {
-    tr_status s = tr_reduce(&p->maps[a], p->h_arrays[a].x, TR_F32, p->lens[a], p->ops, p->sums ? p->sums + a : nullptr,
+    tr_status s = tr_reduce(&p->maps[a], p->h_arrays[a].x, p->xt, p->lens[a], p->ops, p->sums ? p->sums + a : nullptr,
                             TR_F64, p->mins ? p->mins + a : nullptr, p->maxs ? p->maxs + a : nullptr, &e);
     if (s) return s;
   }
@@ -544,7 +567,7 @@ tr_status capture(tr_batch_plan* p, bool unbatched, cudaGraphExec_t* out) {
   if (unbatched) {
     const tr_exec e{cs, p->d_reduce_ws, p->reduce_ws_bytes, 0, 0, -1};
     for (int64_t a = 0; a < p->n_arrays && !s; ++a)
-      s = tr_reduce(&p->maps[a], p->h_arrays[a].x, TR_F32, p->lens[a], p->ops, p->sums ? p->sums + a : nullptr, TR_F64,
+      s = tr_reduce(&p->maps[a], p->h_arrays[a].x, p->xt, p->lens[a], p->ops, p->sums ? p->sums + a : nullptr, TR_F64,
                     p->mins ? p->mins + a : nullptr, p->maxs ? p->maxs + a : nullptr, &e);
   } else {
     s = enqueue(p, cs);

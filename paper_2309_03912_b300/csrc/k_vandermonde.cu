@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(kF32Threads) k_vander_fp32(const float* __rest
 }
 
 // ------------------------------------------------------------- tcgen05 split-bf16
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4) ..
+constexpr int kTcWarps = kTcThreads / 32;
 constexpr int kTileM = 128, kTileN = 256, kK = 32;
 constexpr uint32_t kTmemCols = 256;
 // K-major core-matrix layout (bytes): element (row r, k) of a tile at
@@ -100,24 +101,21 @@ constexpr int kMaxTcGrid = 512;                // workspace slots are sized for 
 
 enum { kOutNone = 0, kOutF32 = 1, kOutBf16 = 2 };
 
-// Shared-memory layout of a CTA: NS A parts, NS B parts, FP32 staging (two
-// blocks per warp with a TMA output, one for a reduction without it), BF16
-// staging, mbarrier and TMEM slot.  The request is at least 80 KiB so that at
-// most two CTAs share an SM: two 256-column accumulators fill its 512 TMEM
-// columns.
+// Shared-memory layout of a CTA: NS A parts, NS B parts, one 4 KiB staging
+// block per warp (FP32 for the TMA store and the column reads; the BF16 output
+// block overlays it), mbarrier and TMEM slot.  The request is at least 80 KiB
+// so that at most two CTAs share an SM: two 256-column accumulators fill its
+// 512 TMEM columns.
 template <int NS, int OUT, bool RED>
 struct TcLayout {
   static constexpr uint32_t a = 0;
   static constexpr uint32_t b = NS * kABytes;
-  static constexpr uint32_t f32 = b + NS * kBBytes;
-  static constexpr uint32_t f32_bytes = OUT == kOutF32 ? 4 * 2 * kStageBytes : (RED ? 4 * kStageBytes : 0);
-  static constexpr uint32_t bf = f32 + f32_bytes;
-  static constexpr uint32_t bf_bytes = OUT == kOutBf16 ? 4 * kStageBf16 : 0;
-  static constexpr uint32_t bar = bf + bf_bytes;
+  static constexpr uint32_t stage = b + NS * kBBytes;
+  static constexpr uint32_t bar = stage + kTcWarps * kStageBytes;
   static constexpr uint32_t used = bar + 64;
   static constexpr uint32_t request = used + 1024 > 80 * 1024 ? used + 1024 : 80 * 1024;
   static_assert(request <= 110 * 1024, "two CTAs per SM");
-  static_assert(!RED || f32_bytes >= 4 * 8 * 32 * 16, "room for the column combination");
+  static_assert(kTcWarps * kStageBytes >= kTcWarps * 4 * 32 * sizeof(double) * 2, "room for the column combination");
 };
 
 // Per-column partial result of one CTA (one workspace slot entry).
@@ -205,23 +203,26 @@ __device__ __forceinline__ uint4 pack_bf16x8(const float* v) {
 // Split v into NS bf16 parts (v = p0 + p1 + ..., each remainder exact in FP32)
 // and store them in K-major core-matrix layout for row `r` of tiles starting at
 // part[0], part[0] + stride, ...
-template <int NS>
+// Only the k-chunks [KC0, KC0 + NKC) of 8 powers each are written (the row's
+// two halves can be written by two threads).
+template <int NS, int KC0 = 0, int NKC = kK / 8>
 __device__ __forceinline__ void store_split_row(unsigned char* part0, uint32_t stride, int r, const float* v) {
-  float rem[kK];
+  constexpr int k0 = KC0 * 8, nk = NKC * 8;
+  float rem[nk];
 #pragma unroll
-  for (int k = 0; k < kK; ++k) rem[k] = v[k];
+  for (int k = 0; k < nk; ++k) rem[k] = v[k0 + k];
   const uint32_t row_off = (uint32_t)(r / 8) * kSBO + (uint32_t)(r % 8) * 16;
 #pragma unroll
   for (int p = 0; p < NS; ++p) {
-    float h[kK];
+    float h[nk];
 #pragma unroll
-    for (int k = 0; k < kK; ++k) {
+    for (int k = 0; k < nk; ++k) {
       h[k] = __bfloat162float(__float2bfloat16_rn(rem[k]));
       rem[k] = rem[k] - h[k];  // exact in FP32
     }
 #pragma unroll
-    for (int kc = 0; kc < kK / 8; ++kc)
-      *reinterpret_cast<uint4*>(part0 + p * stride + row_off + kc * kLBO) = pack_bf16x8(h + 8 * kc);
+    for (int kc = 0; kc < NKC; ++kc)
+      *reinterpret_cast<uint4*>(part0 + p * stride + row_off + (KC0 + kc) * kLBO) = pack_bf16x8(h + 8 * kc);
   }
 }
 
@@ -231,7 +232,7 @@ __host__ __device__ __forceinline__ int64_t tc_tile_begin(int64_t tiles, int64_t
 }
 
 template <int NS, int OUT, bool RED>
-__global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_constant__ CUtensorMap ymap,
+__global__ void __launch_bounds__(kTcThreads, 2) k_vander_tc(const __grid_constant__ CUtensorMap ymap,
                                                              const float* __restrict__ x, int64_t m,
                                                              const float* __restrict__ coef, int deg, int64_t npoly,
                                                              __nv_bfloat16* __restrict__ ybf, ColPart* parts,
@@ -241,8 +242,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   unsigned char* sA = base + L::a;
   unsigned char* sB = base + L::b;
-  unsigned char* sF = base + L::f32;  // 1024-byte aligned (part sizes are multiples of 8 KiB)
-  unsigned char* sH = base + L::bf;
+  unsigned char* sF = base + L::stage;  // 1024-byte aligned (part sizes are multiples of 8 KiB)
   uint64_t* mbar = reinterpret_cast<uint64_t*>(base + L::bar);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
 
@@ -267,15 +267,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  // running column results of this lane: column 32 c + lane of the current column tile, over
-  // the rows of this warp's 32 TMEM lanes of every row tile seen so far
-  float cs_hi[8], cs_lo[8], cmn[8], cmx[8];
+  // warp w works on TMEM lanes (rows) 32 (w % 4) .. + 31 and on the column half w / 4 of the tile
+  const int lane_grp = warp & 3, half = warp >> 2;
+  // running column results of this lane: column 128 half + 32 c + lane of the current column
+  // tile, over this warp's rows of every row tile seen so far
+  float cs_hi[4], cs_lo[4], cmn[4], cmx[4];
   auto reset_cols = [&]() {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) cs_hi[c] = cs_lo[c] = 0.0f, cmn[c] = INFINITY, cmx[c] = -INFINITY;
+    for (int c = 0; c < 4; ++c) cs_hi[c] = cs_lo[c] = 0.0f, cmn[c] = INFINITY, cmx[c] = -INFINITY;
   };
-  // the CTA's results for column tile nt into its workspace slot (CTA + nt): warps combined in
-  // FP64, in warp order, through the FP32 staging (every TMA store has finished reading it)
+  // the CTA's results for column tile nt into its workspace slot (CTA + nt): the four row warps
+  // of each column combined in FP64, in row order, through the staging blocks (every TMA store
+  // has finished reading them)
   auto flush_cols = [&](int64_t nt) {
     if constexpr (OUT == kOutF32) {
       if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -283,21 +286,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
     __syncthreads();
     ColPart* cp = reinterpret_cast<ColPart*>(sF);  // [warp][c][lane]
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
-      cp[(warp * 8 + c) * 32 + lane] = ColPart{(double)cs_hi[c] + (double)cs_lo[c], cmn[c], cmx[c]};
+    for (int c = 0; c < 4; ++c)
+      cp[(warp * 4 + c) * 32 + lane] = ColPart{(double)cs_hi[c] + (double)cs_lo[c], cmn[c], cmx[c]};
     __syncthreads();
-    ColPart* slot = parts + (blockIdx.x + nt) * kTileN;
-    for (int col = tid; col < kTileN; col += kTcThreads) {
-      const int c = col / 32, l = col % 32;
+    {
+      const int col = tid, h = col / 128, c = (col % 128) / 32, l = col % 32;  // kTcThreads == kTileN
       double sum = 0.0;
       float mn = INFINITY, mx = -INFINITY;
-      for (int w = 0; w < 4; ++w) {
-        const ColPart q = cp[(w * 8 + c) * 32 + l];
+      for (int g = 0; g < 4; ++g) {
+        const ColPart q = cp[((h * 4 + g) * 4 + c) * 32 + l];
         sum += q.sum;
         mn = fminf(mn, q.mn);
         mx = fmaxf(mx, q.mx);
       }
-      slot[col] = ColPart{sum, mn, mx};
+      parts[(blockIdx.x + nt) * kTileN + col] = ColPart{sum, mn, mx};
     }
     __syncthreads();
     reset_cols();
@@ -314,24 +316,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
       if constexpr (RED) {
         if (loaded_n >= 0) flush_cols(loaded_n);
       }
-      // C tile: columns n0 .. n0+255 (zero beyond npoly), powers 0 .. 31 (zero beyond deg)
-      for (int half = 0; half < 2; ++half) {
-        const int r = tid + half * kTcThreads;
-        const bool in = n0 + r < npoly;
+      // C tile: columns n0 .. n0+255 (zero beyond npoly), powers 0 .. 31 (zero beyond deg), one
+      // column per thread
+      {
+        const bool in = n0 + tid < npoly;
         float v[kK];
 #pragma unroll
-        for (int k = 0; k < kK; ++k) v[k] = (in && k <= deg) ? __ldg(&coef[(int64_t)k * npoly + n0 + r]) : 0.0f;
-        store_split_row<NS>(sB, kBBytes, r, v);
+        for (int k = 0; k < kK; ++k) v[k] = (in && k <= deg) ? __ldg(&coef[(int64_t)k * npoly + n0 + tid]) : 0.0f;
+        store_split_row<NS>(sB, kBBytes, tid, v);
       }
       loaded_n = nt;
     }
-    {  // V tile: the powers of point m0 + tid by repeated FP32 multiplication, zero above deg
-      const float xi = m0 + tid < m ? __ldg(&x[m0 + tid]) : 0.0f;
+    {  // V tile: the powers of point m0 + tid % 128 by repeated FP32 multiplication, zero above
+       // deg; the two halves of the block write powers 0..15 and 16..31
+      const int r = tid & (kTileM - 1);
+      const float xi = m0 + r < m ? __ldg(&x[m0 + r]) : 0.0f;
       float v[kK];
       v[0] = 1.0f;
 #pragma unroll
       for (int k = 1; k < kK; ++k) v[k] = k <= deg ? v[k - 1] * xi : 0.0f;
-      store_split_row<NS>(sA, kABytes, tid, v);
+      if (tid < kTileM)
+        store_split_row<NS, 0, 2>(sA, kABytes, r, v);
+      else
+        store_split_row<NS, 2, 2>(sA, kABytes, r, v);
     }
     fence_async_smem();  // generic-proxy smem writes -> tensor core
     __syncthreads();
@@ -362,24 +369,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31; 64 columns per TMEM load, handled as
-    // two 32 x 32 blocks; the steps are unrolled so that the running column results stay in
-    // registers and the blocks' dependency chains overlap
-    const int64_t row0 = m0 + warp * 32;
+    // epilogue: warp w reads its 32 TMEM lanes (rows 32 (w % 4) ..) for the 128 columns of its
+    // half, 64 columns per TMEM load handled as two 32 x 32 blocks; the steps are unrolled so that
+    // the running column results stay in registers and the blocks' dependency chains overlap
+    const int64_t row0 = m0 + lane_grp * 32;
     const int valid_rows = (int)imax<int64_t>(0, imin<int64_t>(32, m - row0));
+    unsigned char* stg = sF + (uint32_t)warp * kStageBytes;
 #pragma unroll
-    for (int cp = 0; cp < kTileN / 64; ++cp) {
+    for (int cp = 0; cp < 2; ++cp) {
       float v64[64];
-      tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cp * 64), v64);
+      tmem_ld64(tmem + ((uint32_t)(lane_grp * 32) << 16) + (uint32_t)(half * 128 + cp * 64), v64);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = 2 * cp + h;
-        const float* v = v64 + 32 * h;
-        const int64_t col0 = n0 + c * 32;
+      for (int hh = 0; hh < 2; ++hh) {
+        const int c = 2 * cp + hh;  // block of this warp's half
+        const float* v = v64 + 32 * hh;
+        const int64_t col0 = n0 + half * 128 + c * 32;
         if constexpr (OUT == kOutF32 || RED) {
           // row `lane`'s 16-byte chunk q at chunk q ^ (lane % 8): the 128-byte swizzle of the tensor map
-          unsigned char* stg = sF + (uint32_t)(OUT == kOutF32 ? warp * 2 + (c & 1) : warp) * kStageBytes;
-          if (OUT == kOutF32 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          if (OUT == kOutF32 && lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
           __syncwarp();
 #pragma unroll
           for (int q = 0; q < 8; ++q)
@@ -388,14 +395,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
             fence_async_smem();
             __syncwarp();
             if (lane == 0) {
-              if (valid_rows > 0 && col0 < npoly)
+              if (valid_rows > 0 && col0 < npoly) {
                 asm volatile(
                     "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(&ymap),
                     "r"((int)col0), "r"((int)row0), "r"(smem_u32(stg))
                     : "memory");
-              // one bulk group per block even when the store is skipped (an empty group), so that
-              // "at most one group pending" always means the staging slot written next is free
-              asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+              }
             }
           } else {
             __syncwarp();
@@ -440,18 +446,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_vander_tc(const __grid_consta
           }
         }
         if constexpr (OUT == kOutBf16) {
-          // row `lane`'s four 16-byte chunks (8 bf16 each) at chunk q ^ ((lane / 2) % 4)
-          // (64-byte rows, conflict-free writes); then 8 rows per instruction leave as 16-byte stores
-          unsigned char* hb = sH + (uint32_t)warp * kStageBf16;
+          // row `lane`'s four 16-byte chunks (8 bf16 each) at chunk q ^ ((lane / 2) % 4) of the
+          // warp's staging block (64-byte rows, conflict-free writes; after the column reads);
+          // then 8 rows per instruction leave as 16-byte stores
           __syncwarp();
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            *reinterpret_cast<uint4*>(hb + lane * 64 + ((q ^ ((lane >> 1) & 3)) * 16)) = pack_bf16x8(v + 8 * q);
+            *reinterpret_cast<uint4*>(stg + lane * 64 + ((q ^ ((lane >> 1) & 3)) * 16)) = pack_bf16x8(v + 8 * q);
           __syncwarp();
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int r = i * 8 + (lane >> 2), q = lane & 3;
-            const uint4 w = *reinterpret_cast<const uint4*>(hb + r * 64 + ((q ^ ((r >> 1) & 3)) * 16));
+            const uint4 w = *reinterpret_cast<const uint4*>(stg + r * 64 + ((q ^ ((r >> 1) & 3)) * 16));
             const int64_t col = col0 + q * 8;
             if (r < valid_rows && col < npoly) st_stream(ybf + (row0 + r) * npoly + col, w);
           }

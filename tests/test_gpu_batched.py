@@ -118,3 +118,37 @@ def test_plan_validation(B):
         B.BatchPlan([x], [{"kind": "xorshift32"}], s, None, None, ops=B.TR_SUM)
     with pytest.raises(B.TrError):
         B.BatchPlan([x], [I.simple_map("square")], None, None, None, ops=B.TR_SUM)
+
+
+@pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16], ids=["f16", "bf16"])
+def test_batched_low_precision_storage(orc, B, dt):
+    """FP16 / BF16 storage with FP32 compute: every array against the oracle's
+    binary32 map values of the stored inputs (compensated sums within 1e-6
+    normwise, min / max exact), and equal to the per-array launches of the
+    same storage."""
+    xs, maps = _workload(120, 15)
+    dev = [torch.from_numpy(x).to(dt).cuda() for x in xs]
+    n = len(xs)
+    out = [torch.zeros(n, dtype=torch.float64, device="cuda")] + \
+          [torch.zeros(n, dtype=torch.float32, device="cuda") for _ in range(2)]
+    plan = B.BatchPlan(dev, maps, *out, autotune=False)
+    plan.run()
+    torch.cuda.synchronize()
+    s, lo, hi = (t.cpu().numpy() for t in out)
+    for a, (x, m) in enumerate(zip(dev, maps)):
+        xv = x.cpu().double().numpy()
+        rs, rlo, rhi, ra = orc.reduce_float_mt(oracle_map(orc, m), xv, 1, f32=True)
+        assert abs(s[a] - rs) <= 1e-6 * ra + 1e-30, (a, m["kind"])
+        if xv.size:
+            assert lo[a] == rlo and hi[a] == rhi, a
+    ref = [torch.zeros_like(t) for t in out]
+    plan2 = B.BatchPlan(dev, maps, *ref, autotune=False)
+    plan2.run_unbatched(False)
+    torch.cuda.synchronize()
+    assert torch.equal(out[1], ref[1]) and torch.equal(out[2], ref[2])  # min / max: same values
+    s2 = ref[0].cpu().numpy()
+    for a, (x, m) in enumerate(zip(dev, maps)):
+        rs, _, _, ra = orc.reduce_float_mt(oracle_map(orc, m), x.cpu().double().numpy(), 1, f32=True)
+        assert abs(s2[a] - rs) <= 1e-6 * ra + 1e-30, a
+    plan.close()
+    plan2.close()

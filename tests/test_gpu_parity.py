@@ -487,3 +487,43 @@ def test_segreduce_offset_ends_reported(orc, B, misaligned, case):
     assert e.value.status == 7
     B.tr_workspace_init(ws)
     check_seg(orc, m, xh, off, segreduce_dev(B, m, x, off))
+
+
+def test_segreduce_host_buffers_equal_device_call(B):
+    """tr_segmented_reduce_host (host buffers in and out, the copies enqueued by
+    the call) gives the device call's results bit for bit, from page-locked and
+    from pageable host memory; missing buffers are argument errors."""
+    import ctypes
+    m = MAPS[4]
+    n = 3_000_017
+    th, _ = host_input("f32", n, seed=41)
+    off = offsets_random(n, 500, seed=41)
+    nseg = off.size - 1
+    ref = segreduce_dev(B, m, th.cuda(), off)
+    L = B.lib()
+    md = B.MapDesc(m)
+    xd = torch.empty(n, dtype=torch.float32, device="cuda")
+    offd = torch.empty(nseg + 1, dtype=torch.int64, device="cuda")
+    sd = torch.empty(nseg, dtype=torch.float64, device="cuda")
+    lod = torch.empty(nseg, dtype=torch.float32, device="cuda")
+    hid = torch.empty(nseg, dtype=torch.float32, device="cuda")
+    ws = B.workspace(B.tr_segmented_reduce_workspace_size(n, nseg, B.TR_F32))
+    ex = B.make_exec(ws)
+    for pinned in (True, False):
+        xh = th.pin_memory() if pinned else th.clone()
+        offh = torch.from_numpy(off).pin_memory() if pinned else torch.from_numpy(off.copy())
+        outs = [torch.zeros(nseg, dtype=dt) for dt in (torch.float64, torch.float32, torch.float32)]
+        if pinned:
+            outs = [o.pin_memory() for o in outs]
+        st = L.tr_segmented_reduce_host(md.ref(), xh.data_ptr(), B.TR_F32, n, offh.data_ptr(), nseg, 7,
+                                        outs[0].data_ptr(), B.TR_F64, outs[1].data_ptr(), outs[2].data_ptr(),
+                                        xd.data_ptr(), offd.data_ptr(), sd.data_ptr(), lod.data_ptr(), hid.data_ptr(),
+                                        ctypes.byref(ex))
+        assert st == 0, L.tr_last_error()
+        B.tr_check(ex)
+        for got, want in zip(outs, ref):
+            assert np.array_equal(got.double().numpy(), want)
+    st = L.tr_segmented_reduce_host(md.ref(), th.data_ptr(), B.TR_F32, n, None, nseg, 7, None, B.TR_F64, None,
+                                    None, xd.data_ptr(), offd.data_ptr(), sd.data_ptr(), lod.data_ptr(),
+                                    hid.data_ptr(), ctypes.byref(ex))
+    assert st == 1

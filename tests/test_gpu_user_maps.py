@@ -43,7 +43,7 @@ def U():
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
     pkg = os.path.dirname(build.LIB)
     cmd = ([build.NVCC] + build.FLAGS + ["--extended-lambda", "-shared", SRC, "-o", OUT, "-L" + pkg, "-ltr",
-                                         "-Xlinker", "-rpath=" + pkg])
+                                         "-Xlinker", "-rpath=" + pkg] + build.LINK)
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     L = ctypes.CDLL(OUT)
