@@ -46,9 +46,9 @@ NSEG_HEAD = 65536
 WORKLOAD = ("segmented transform-reduce: N=2^28 f32 x~N(0,1), f = rational P/Q deg 6/6 (Q even, positive "
             "coefficients), 65536 segments with lengths U{1..8192} scaled to N; per segment compensated "
             "sum (f64 out), min, max")
-SEG_SOURCES = ["paper_2309_03912_b300/csrc/k_segreduce.cu", "paper_2309_03912_b300/csrc/accum.cuh",
-               "paper_2309_03912_b300/csrc/range.cuh", "paper_2309_03912_b300/csrc/dispatch.cuh",
-               "paper_2309_03912_b300/csrc/common.cuh", "paper_2309_03912_b300/csrc/maps.h"]
+SEG_SOURCES = ["paper_2309_03912_b300/csrc/" + f for f in (
+    "k_segreduce.cu", "segreduce_kernel.cuh", "accum.cuh", "range.cuh", "dispatch.cuh", "internal.h",
+    "common.cuh", "maps.h", "hd.h")]
 
 
 def parse():

@@ -200,29 +200,42 @@ __device__ __forceinline__ uint4 pack_bf16x8(const float* v) {
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+// Two floats as bf16x2 (round to nearest even): `hi` in the upper half.
+__device__ __forceinline__ uint32_t cvt_bf16x2(float hi, float lo) {
+  uint32_t d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+
 // Split v into NS bf16 parts (v = p0 + p1 + ..., each remainder exact in FP32)
 // and store them in K-major core-matrix layout for row `r` of tiles starting at
-// part[0], part[0] + stride, ...
+// part[0], part[0] + stride, ...  Powers are handled in pairs: one packed
+// conversion rounds both, the pair word is stored as is, and its two bf16
+// values (widened by shifts) leave the remainders by one packed subtraction.
 // Only the k-chunks [KC0, KC0 + NKC) of 8 powers each are written (the row's
 // two halves can be written by two threads).
 template <int NS, int KC0 = 0, int NKC = kK / 8>
 __device__ __forceinline__ void store_split_row(unsigned char* part0, uint32_t stride, int r, const float* v) {
-  constexpr int k0 = KC0 * 8, nk = NKC * 8;
-  float rem[nk];
+  constexpr int k0 = KC0 * 8, np = NKC * 4;  // pairs of powers
+  unsigned long long rem[np];
 #pragma unroll
-  for (int k = 0; k < nk; ++k) rem[k] = v[k0 + k];
+  for (int i = 0; i < np; ++i) rem[i] = pack_f32x2(v[k0 + 2 * i], v[k0 + 2 * i + 1]);
   const uint32_t row_off = (uint32_t)(r / 8) * kSBO + (uint32_t)(r % 8) * 16;
 #pragma unroll
   for (int p = 0; p < NS; ++p) {
-    float h[nk];
+    uint32_t w[np];
 #pragma unroll
-    for (int k = 0; k < nk; ++k) {
-      h[k] = __bfloat162float(__float2bfloat16_rn(rem[k]));
-      rem[k] = rem[k] - h[k];  // exact in FP32
+    for (int i = 0; i < np; ++i) {
+      float lo, hi;
+      unpack_f32x2(rem[i], lo, hi);
+      w[i] = cvt_bf16x2(hi, lo);
+      if (p + 1 < NS)  // exact in FP32
+        rem[i] = sub_f32x2(rem[i], pack_f32x2(__uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xFFFF0000u)));
     }
 #pragma unroll
     for (int kc = 0; kc < NKC; ++kc)
-      *reinterpret_cast<uint4*>(part0 + p * stride + row_off + (KC0 + kc) * kLBO) = pack_bf16x8(h + 8 * kc);
+      *reinterpret_cast<uint4*>(part0 + p * stride + row_off + (KC0 + kc) * kLBO) =
+          make_uint4(w[4 * kc], w[4 * kc + 1], w[4 * kc + 2], w[4 * kc + 3]);
   }
 }
 
@@ -309,6 +322,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_vander_tc(const __grid_consta
   uint32_t phase = 0;
   int64_t loaded_n = -1;
   bool ok = true;
+  // point m0 + tid % 128 of a tile, loaded one tile ahead so that its latency hides behind the
+  // products and the epilogue of the tile before
+  auto load_x = [&](int64_t t) {
+    const int64_t i = (t % m_tiles) * kTileM + (tid & (kTileM - 1));
+    return t < t_end && i < m ? __ldg(&x[i]) : 0.0f;
+  };
+  float x_next = load_x(t_begin);
   for (int64_t t = t_begin; t < t_end && ok; ++t) {
     const int64_t nt = t / m_tiles, mt = t % m_tiles;
     const int64_t m0 = mt * kTileM, n0 = nt * kTileN;
@@ -330,7 +350,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_vander_tc(const __grid_consta
     {  // V tile: the powers of point m0 + tid % 128 by repeated FP32 multiplication, zero above
        // deg; the two halves of the block write powers 0..15 and 16..31
       const int r = tid & (kTileM - 1);
-      const float xi = m0 + r < m ? __ldg(&x[m0 + r]) : 0.0f;
+      const float xi = x_next;
+      x_next = load_x(t + 1);
       float v[kK];
       v[0] = 1.0f;
 #pragma unroll
@@ -479,19 +500,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_vander_tc(const __grid_consta
 }
 
 // Second launch of the column reduction: thread j joins column j's slots in CTA
-// order (the CTAs whose tile range meets column tile j / 256), in FP64.
-__global__ void __launch_bounds__(256) k_vander_cols(const ColPart* __restrict__ parts, int64_t m_tiles,
-                                                     int64_t tiles, int64_t grid, int64_t npoly, float* colsum,
-                                                     float* colmin, float* colmax) {
+// order (the CTAs whose tile range meets j's column block of `width` columns,
+// blocks_per_col tiles per column block), in FP64.  Slot (CTA c, column block
+// nt) lives at (c + nt) * width: a CTA's tile range is contiguous in
+// column-block-major order, so no two (c, nt) it meets share c + nt.
+__global__ void __launch_bounds__(256) k_vander_join(const ColPart* __restrict__ parts, int64_t blocks_per_col,
+                                                     int64_t tiles, int64_t grid, int64_t width, int64_t npoly,
+                                                     float* colsum, float* colmin, float* colmax) {
   const int64_t j = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (j >= npoly) return;
-  const int64_t nt = j / kTileN, lo = nt * m_tiles, hi = lo + m_tiles;
+  const int64_t nt = j / width, lo = nt * blocks_per_col, hi = lo + blocks_per_col;
   double sum = 0.0;
   float mn = INFINITY, mx = -INFINITY;
   for (int64_t c = 0; c < grid; ++c) {
     const int64_t tb = tc_tile_begin(tiles, c, grid), te = tc_tile_begin(tiles, c + 1, grid);
     if (te <= lo || tb >= hi || tb == te) continue;
-    const ColPart q = parts[(c + nt) * kTileN + j % kTileN];
+    const ColPart q = parts[(c + nt) * width + j % width];
     sum += q.sum;
     mn = fminf(mn, q.mn);
     mx = fmaxf(mx, q.mx);
@@ -499,6 +523,216 @@ __global__ void __launch_bounds__(256) k_vander_cols(const ColPart* __restrict__
   if (colsum) colsum[j] = (float)sum;
   if (colmin) colmin[j] = mn;
   if (colmax) colmax[j] = mx;
+}
+
+// ---- the column results alone: the transposed product ----------------------
+//
+// Without a Y output the product is formed transposed, Y^T = C^T V^T, tile by
+// tile: 128 polynomials (the M side: the C tile, K-major) by 256 points (the N
+// side: the V tile, K-major).  The accumulator's TMEM lanes are then
+// polynomials and its columns points, so a thread owns one polynomial of its
+// warp's lanes and folds that polynomial's values at the warp's 128 points
+// into its running compensated sum, minimum and maximum in registers -- no
+// shared memory and no exchange between lanes.  A CTA walks its tiles
+// polynomial-block-major, so the running results carry over all of its point
+// blocks, and are written to the CTA's workspace slot when the block changes.
+constexpr int kPolyBlk = 128, kPtBlk = 256;
+
+template <int NS>
+struct ColLayout {
+  static constexpr uint32_t a = 0;                   // C parts: NS x 128 polynomials x 32 powers
+  static constexpr uint32_t b = NS * kABytes;        // V parts: NS x 256 points x 32 powers
+  static constexpr uint32_t comb = b + NS * kBBytes; // the warps' halves combined: 4 x 32 ColPart
+  static constexpr uint32_t bar = comb + 4 * 32 * sizeof(ColPart);
+  static constexpr uint32_t used = bar + 64;
+  static constexpr uint32_t request = used + 1024 > 80 * 1024 ? used + 1024 : 80 * 1024;
+  static_assert(request <= 110 * 1024, "two CTAs per SM");
+};
+
+// min / max / sum of 64 values: four independent min3 / max3 chains, pairwise sums
+__device__ __forceinline__ void stats64(const float* v, float& mn, float& mx, float& sum) {
+  float a[4], b[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    a[c] = fminf(v[16 * c], v[16 * c + 1]);
+    b[c] = fmaxf(v[16 * c], v[16 * c + 1]);
+#pragma unroll
+    for (int r = 2; r < 16; r += 2) {
+      a[c] = min3f(a[c], v[16 * c + r], v[16 * c + r + 1]);
+      b[c] = max3f(b[c], v[16 * c + r], v[16 * c + r + 1]);
+    }
+  }
+  mn = min3f(min3f(a[0], a[1], a[2]), a[3], a[3]);
+  mx = max3f(max3f(b[0], b[1], b[2]), b[3], b[3]);
+  sum = pairwise<64>(v);
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kTcThreads, 2) k_vander_colred(const float* __restrict__ x, int64_t m,
+                                                                 const float* __restrict__ coef, int deg,
+                                                                 int64_t npoly, ColPart* parts, WsHeader* hdr) {
+  using L = ColLayout<NS>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
+  unsigned char* sA = base + L::a;
+  unsigned char* sB = base + L::b;
+  ColPart* comb = reinterpret_cast<ColPart*>(base + L::comb);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(base + L::bar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = warp & 3, h = warp >> 2;  // TMEM lanes 32 g .. (polynomials), point half h
+  const int64_t m_blocks = (m + kPtBlk - 1) / kPtBlk, p_blocks = (npoly + kPolyBlk - 1) / kPolyBlk;
+  const int64_t tiles = m_blocks * p_blocks;
+  const int64_t t_begin = tc_tile_begin(tiles, blockIdx.x, gridDim.x),
+                t_end = tc_tile_begin(tiles, blockIdx.x + 1, gridDim.x);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(mbar), 1);
+    mbar_init_fence();
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  // running results of polynomial 128 pb + 32 g + lane over the points of half h seen so far
+  float cs_hi = 0.0f, cs_lo = 0.0f, cmn = INFINITY, cmx = -INFINITY;
+  auto flush = [&](int64_t pb) {  // both halves combined in FP64 into the slot (CTA + pb)
+    if (h == 1) comb[g * 32 + lane] = ColPart{(double)cs_hi + (double)cs_lo, cmn, cmx};
+    __syncthreads();
+    if (h == 0) {
+      const ColPart q = comb[g * 32 + lane];
+      parts[(blockIdx.x + pb) * kPolyBlk + g * 32 + lane] =
+          ColPart{((double)cs_hi + (double)cs_lo) + q.sum, fminf(cmn, q.mn), fmaxf(cmx, q.mx)};
+    }
+    __syncthreads();
+    cs_hi = cs_lo = 0.0f;
+    cmn = INFINITY;
+    cmx = -INFINITY;
+  };
+
+  uint32_t phase = 0;
+  int64_t loaded_p = -1;
+  bool ok = true;
+  // point i0 + tid of a tile, loaded one tile ahead (its latency hides behind the tile before)
+  auto load_x = [&](int64_t t) {
+    const int64_t i = (t % m_blocks) * kPtBlk + tid;
+    return t < t_end && i < m ? __ldg(&x[i]) : 0.0f;
+  };
+  float x_next = load_x(t_begin);
+  for (int64_t t = t_begin; t < t_end && ok; ++t) {
+    const int64_t pb = t / m_blocks, qb = t % m_blocks;
+    const int64_t j0 = pb * kPolyBlk, i0 = qb * kPtBlk;
+    if (pb != loaded_p) {
+      if (loaded_p >= 0) flush(loaded_p);
+      if (tid < kPolyBlk) {  // C tile: polynomial j0 + tid (zero beyond npoly), powers 0 .. 31 (zero beyond deg)
+        const bool in = j0 + tid < npoly;
+        float v[kK];
+#pragma unroll
+        for (int k = 0; k < kK; ++k) v[k] = (in && k <= deg) ? __ldg(&coef[(int64_t)k * npoly + j0 + tid]) : 0.0f;
+        store_split_row<NS>(sA, kABytes, tid, v);
+      }
+      loaded_p = pb;
+    }
+    {  // V tile: the powers of point i0 + tid (zero beyond m) by repeated FP32 multiplication, zero above deg
+      const float xi = x_next;
+      x_next = load_x(t + 1);
+      float v[kK];
+      v[0] = 1.0f;
+#pragma unroll
+      for (int k = 1; k < kK; ++k) v[k] = k <= deg ? v[k - 1] * xi : 0.0f;
+      store_split_row<NS>(sB, kBBytes, tid, v);
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      bool first = true;
+#pragma unroll
+      for (int d = 0; d < NS; ++d)
+#pragma unroll
+        for (int i = 0; i <= d; ++i) {
+          const uint32_t ai = a0 + i * kABytes, bj = b0 + (d - i) * kBBytes;
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            mma_bf16(tmem, smem_desc(ai + s * 2 * kLBO), smem_desc(bj + s * 2 * kLBO), first ? 0u : 1u);
+            first = false;
+          }
+        }
+      mma_commit(smem_u32(mbar));
+    }
+    if (!mbar_wait_until(smem_u32(mbar), phase, kMmaWaitNs)) ok = false;
+    phase ^= 1u;
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+      ok = false;
+      if (tid == 0) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)t);
+      break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // this thread's polynomial at the 128 points of half h, 64 per TMEM load
+    const int valid = (int)imax<int64_t>(0, imin<int64_t>(128, m - (i0 + h * 128)));
+#pragma unroll
+    for (int cp = 0; cp < 2; ++cp) {
+      float v[64];
+      tmem_ld64(tmem + ((uint32_t)(g * 32) << 16) + (uint32_t)(h * 128 + cp * 64), v);
+      float tmn, tmx, ts;
+      if (valid >= (cp + 1) * 64) {
+        stats64(v, tmn, tmx, ts);
+      } else {  // points beyond m are left out (the last point block only)
+#pragma unroll
+        for (int r = 0; r < 64; ++r) v[r] = cp * 64 + r < valid ? v[r] : NAN;
+        tmn = INFINITY;
+        tmx = -INFINITY;
+#pragma unroll
+        for (int r = 0; r < 64; ++r) {
+          tmn = fminf(tmn, v[r]);  // NaN (left out) is ignored
+          tmx = fmaxf(tmx, v[r]);
+          v[r] = v[r] == v[r] ? v[r] : 0.0f;
+        }
+        ts = pairwise<64>(v);
+      }
+      const float yk = ts - (-cs_lo);  // compensated running sum (Kahan)
+      const float tt = cs_hi + yk;
+      cs_lo = -((tt - cs_hi) - yk);
+      cs_hi = tt;
+      cmn = fminf(cmn, tmn);
+      cmx = fmaxf(cmx, tmx);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // TMEM and the A / B tiles are free for the next tile
+  }
+  if (ok && loaded_p >= 0) flush(loaded_p);
+  if (!ok) mbar_wait_until(smem_u32(mbar), phase ^ 1u, kMmaWaitNs);  // let committed products drain
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+template <int NS>
+tr_status launch_colred(const float* x, int64_t m, const float* coef, int deg, int64_t npoly, float* colsum,
+                        float* colmin, float* colmax, const tr_exec* e) {
+  using L = ColLayout<NS>;
+  auto kern = k_vander_colred<NS>;
+  tr_status s = ensure_dyn_smem((const void*)kern, (int)L::request, "cudaFuncSetAttribute(k_vander_colred)");
+  if (s) return s;
+  const int64_t m_blocks = ceil_div(m, kPtBlk), tiles = m_blocks * ceil_div(npoly, kPolyBlk);
+  const int64_t grid = std::min<int64_t>(std::min<int64_t>(tiles, 2 * (int64_t)dev_info().sm_count), kMaxTcGrid);
+  ColPart* parts = reinterpret_cast<ColPart*>(ws_body(e));
+  cudaStream_t st = stream_of(e);
+  kern<<<(unsigned)grid, kTcThreads, L::request, st>>>(x, m, coef, deg, npoly, parts, ws_header(e));
+  if ((s = launch_status("k_vander_colred"))) return s;
+  k_vander_join<<<(unsigned)ceil_div(npoly, 256), 256, 0, st>>>(parts, m_blocks, tiles, grid, kPolyBlk, npoly, colsum,
+                                                               colmin, colmax);
+  return launch_status("k_vander_join");
 }
 
 template <int NS, int OUT, bool RED>
@@ -516,9 +750,9 @@ tr_status launch_tc(const CUtensorMap& ymap, const float* x, int64_t m, const fl
                                                        static_cast<__nv_bfloat16*>(y), parts, ws_header(e));
   if ((s = launch_status("k_vander_tc"))) return s;
   if constexpr (RED) {
-    k_vander_cols<<<(unsigned)ceil_div(npoly, 256), 256, 0, st>>>(parts, m_tiles, tiles, grid, npoly, colsum, colmin,
-                                                                 colmax);
-    return launch_status("k_vander_cols");
+    k_vander_join<<<(unsigned)ceil_div(npoly, 256), 256, 0, st>>>(parts, m_tiles, tiles, grid, kTileN, npoly, colsum,
+                                                                 colmin, colmax);
+    return launch_status("k_vander_join");
   }
   return TR_OK;
 }
@@ -530,11 +764,13 @@ tr_status launch_tc_ns(int out, bool red, const CUtensorMap& ymap, const float* 
                                  : launch_tc<NS, kOutF32, false>(ymap, x, m, coef, deg, npoly, y, cs, cn, cx, e);
   if (out == kOutBf16) return red ? launch_tc<NS, kOutBf16, true>(ymap, x, m, coef, deg, npoly, y, cs, cn, cx, e)
                                   : launch_tc<NS, kOutBf16, false>(ymap, x, m, coef, deg, npoly, y, cs, cn, cx, e);
-  return launch_tc<NS, kOutNone, true>(ymap, x, m, coef, deg, npoly, y, cs, cn, cx, e);
+  return launch_colred<NS>(x, m, coef, deg, npoly, cs, cn, cx, e);  // column results alone
 }
 
+// Slots of either form: (grid + column blocks) x block width, at most
+// (kMaxTcGrid + npoly / 128 + 1) x 256 entries.
 size_t vander_ws_bytes(int64_t npoly) {
-  return (size_t)kWsHeader + (size_t)(kMaxTcGrid + ceil_div(std::max<int64_t>(npoly, 1), kTileN)) * kTileN *
+  return (size_t)kWsHeader + (size_t)(kMaxTcGrid + ceil_div(std::max<int64_t>(npoly, 1), kPolyBlk)) * kTileN *
                                  sizeof(ColPart);
 }
 

@@ -146,7 +146,7 @@ def test_column_results(orc, B, prec, out, m, npoly):
         # the column results are those of the written Y (same FP32 tile values)
         yy = y.cpu().numpy().astype(np.float64)
         assert np.array_equal(cols[1], yy.min(axis=0)) and np.array_equal(cols[2], yy.max(axis=0))
-    _, again = run(B, x, C, prec, out=None, cols=True)
+    _, again = run(B, x, C, prec, out=dt, cols=True)
     assert all(np.array_equal(a, b) for a, b in zip(cols, again))  # deterministic
 
 
@@ -180,7 +180,8 @@ def test_identity_and_binomial(orc, B):
 
 def test_persistent_tiles_and_column_reload(orc, B):
     """More tiles than CTAs and several column tiles per CTA range, with and
-    without output."""
+    without output (without Y the transposed product walks 128-polynomial
+    blocks, several per CTA range as well)."""
     m, npoly = 128 * 700, 768
     g = np.random.default_rng(11)
     x = g.uniform(-1, 1, m).astype(np.float32)
@@ -193,6 +194,11 @@ def test_persistent_tiles_and_column_reload(orc, B):
     assert np.array_equal(cols[1], yy.min(axis=0)) and np.array_equal(cols[2], yy.max(axis=0))
     s_from_y = np.array([math.fsum(yy[:, j]) for j in range(npoly)])
     assert np.all(np.abs(cols[0] - s_from_y) <= 1e-6 * np.abs(yy).sum(axis=0))
+    for prec in (0, 2):
+        _, alone = run(B, x, C, prec, out=None, cols=True)
+        es, emn, emx = _check_cols(orc, x, C, alone, BAR[prec])
+        print(f"precision {prec}, column results alone, {m}x{npoly}: sum {es:.3g}, min {emn:.3g}, max {emx:.3g}")
+        assert es <= BAR[prec] and emn <= BAR[prec] and emx <= BAR[prec], (es, emn, emx)
 
 
 def _dyadic_power_sums(N, deg):

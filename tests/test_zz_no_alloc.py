@@ -5,9 +5,10 @@ handed only input and output pointers, or loops that must not allocate once
 started cannot supply a workspace; tr_scan_noalloc keeps its scratch in a
 fixed array inside the library instead.  This test calls it through the C ABI
 twice in a row (the second call finds the first call's leftovers in the shared
-array) and checks its output against tr_scan's with the tolerances used by the
-other scan tests: bit for bit for integer scans, 1e-5 relative for the
-compensated f32 scan of x^2 >= 0.  It also checks that sizes beyond the array's
+array) and checks each output against the oracle with the tolerances used by
+the other scan tests: bit for bit for the integer scans (u32 -> u32 mod 2^32
+and u32 -> u64), 1e-5 relative per output for the compensated f32 scan of
+x^2 >= 0 (the oracle's prefixes are exact, rounded once).  It also checks that sizes beyond the array's
 limit are rejected with a message naming the limit.
 
 This file sorts last so that a run stopping at the first failure has run
@@ -19,6 +20,7 @@ import numpy as np
 import pytest
 
 from paper_2309_03912_b300 import inputs as I
+from tests.helpers import u32_host, u64_host
 
 pytestmark = pytest.mark.gpu
 
@@ -37,16 +39,6 @@ def B():
     return binding
 
 
-def _ref_scan(B, m, x, y_dtype):
-    n = x.numel()
-    y = torch.empty(n, dtype=y_dtype, device="cuda")
-    ws = B.workspace(B.tr_scan_workspace_size(n, B.dtype_of(x), B.dtype_of(y)))
-    ex = B.make_exec(ws)
-    B.tr_scan(m, x, y, ex)
-    B.tr_check(ex)
-    return y
-
-
 def _noalloc_twice(B, m, x, y_dtype):
     outs = []
     for _ in range(2):
@@ -60,21 +52,23 @@ def _noalloc_twice(B, m, x, y_dtype):
 
 
 @pytest.mark.parametrize("n", [1, 4097, 3_000_001, LIMIT])
-def test_u32_scans_match_tr_scan_bitwise(B, n):
-    x = torch.from_numpy(I.u32(I.rng("misc", 21), n).view(np.int32)).cuda()
+def test_u32_scans_match_the_oracle_bitwise(orc, B, n):
+    xh = I.u32(I.rng("misc", 21), n)
+    x = torch.from_numpy(xh.view(np.int32)).cuda()
     m = {"kind": "splitmix32"}
-    for y_dtype in (torch.int32, torch.int64):
-        ref = _ref_scan(B, m, x, y_dtype).cpu().numpy()
+    spec = orc.MapSpec("splitmix32")
+    for y_dtype, ref, host in ((torch.int32, orc.scan_u32(spec, xh), u32_host),
+                               (torch.int64, orc.scan_u32_u64(spec, xh), u64_host)):
         for y in _noalloc_twice(B, m, x, y_dtype):
-            assert np.array_equal(y.cpu().numpy(), ref)
+            assert np.array_equal(host(y), ref)
 
 
-def test_f32_scan_matches_tr_scan_within_tolerance(B):
+def test_f32_scan_matches_the_oracle_within_tolerance(orc, B):
     n = 1_000_003
-    x = torch.from_numpy(np.random.default_rng(22).uniform(0, 1, n).astype(np.float32)).cuda()
-    m = I.simple_map("square")
-    ref = _ref_scan(B, m, x, torch.float32).double().cpu().numpy()
-    for y in _noalloc_twice(B, m, x, torch.float32):
+    xh = np.random.default_rng(22).uniform(0, 1, n).astype(np.float32)
+    x = torch.from_numpy(xh).cuda()
+    ref = orc.scan_float(orc.MapSpec("square"), xh, 24)
+    for y in _noalloc_twice(B, I.simple_map("square"), x, torch.float32):
         got = y.double().cpu().numpy()
         assert np.all(np.abs(got - ref) <= 1e-5 * np.abs(ref) + 1e-38)
 
