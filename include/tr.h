@@ -214,7 +214,10 @@ tr_status tr_scan_workspace_size(int64_t n, tr_dtype xt, tr_dtype yt, size_t* by
  *   F16/BF16/F32 -> F32  float-float within a tile, FP64 between tiles, each
  *                 output rounded once from the compensated prefix.
  * d_carry_in (nullable, device, one element of yt's type) is added to every
- * output.  y may equal x when the element sizes match.  Each look-back wait
+ * output.  y may equal x when the element sizes match.  4-byte inputs and
+ * outputs on 16-byte aligned arrays move through the TMA engine; the
+ * workspace holds one 128-byte look-back line per tile of 8,192 elements.
+ * Each look-back wait
  * is bounded by exec->wait_timeout_us; on expiry tr_check returns
  * TR_ERR_TIMEOUT and the output is unspecified.  Float scans may differ in
  * the last bit between runs (where the look-back stops depends on timing). */

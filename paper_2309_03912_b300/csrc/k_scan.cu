@@ -5,6 +5,7 @@
 
 namespace tr {
 
+// One look-back line per tile of 8,192 elements.
 size_t scan_ws_bytes(int64_t n, tr_dtype, tr_dtype) {
   const int64_t tiles = std::max<int64_t>(1, ceil_div(n, scank::kTile));
   return (size_t)(kWsHeader + tiles * scank::kLineBytes);

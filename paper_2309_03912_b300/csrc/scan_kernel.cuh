@@ -5,26 +5,30 @@
 //
 // Single-pass scan with decoupled look-back (Merrill & Garland, "Single-pass
 // parallel prefix scan with decoupled look-back", NVR-2016-002):
-//   * each block takes a tile id from an atomic counter (dynamic ids: every
-//     tile's predecessors have already started, so waiting on them ends);
-//   * lanes load consecutive 128-bit vectors of the tile (coalesced), map
-//     them and park the values in shared memory, one padded row of kItems
-//     contiguous elements per thread; threads total their rows, warps scan the
-//     totals with shuffles and the block combines warp totals;
-//   * the tile publishes its aggregate (flag A), then warp 0 looks back over
-//     32 (128 for u64 carries) predecessors per round,
-//     summing aggregates until it meets an inclusive prefix (flag P), and
-//     publishes its own inclusive prefix.  Each tile's state has its own
-//     128-byte line; u32 and FP64 carries share one 64-bit status word with
-//     their flag (one relaxed load, no fence), a u64 carry sits beside a flag
-//     released after it;
+//   * each block takes tile ids from an atomic counter, at most one tile ahead
+//     of the one it computes (dynamic ids: every tile's predecessors have
+//     already started, so waiting on them ends);
+//   * the tile is mapped and totalled in shared memory (threads total their
+//     rows, warps scan the row totals with shuffles, the block combines warp
+//     totals) and its aggregate is published at once (flag A);
+//   * a dedicated look-back warp reads 256 predecessors per round (128 for u64
+//     carries), summing aggregates until it meets an inclusive prefix (flag P),
+//     publishes the tile's inclusive prefix and hands the exclusive prefix to
+//     the compute warps, which meanwhile work on the next tile.  Each tile's
+//     state has its own 128-byte line; u32 and float-float carries share one
+//     64-bit status word with their flag (one relaxed load, no fence), a u64
+//     carry sits beside a flag released after it;
 //   * every wait is bounded by a %globaltimer deadline and an abort word: on
 //     expiry the block records TR_ERR_TIMEOUT and finishes instead of hanging.
-// Each call clears the look-back lines and the tile counter with two memsets
-// on the stream (graph-capturable) before the kernel.
+// Two kernels share this: k_scan (tiles loaded by the compute warps into
+// registers, any storage and output type) and k_scan_tma (4-byte inputs and
+// outputs on aligned arrays: tiles moved by TMA box loads and stores through a
+// ring of shared-memory stages fed by a producer warp).  Each call clears the
+// look-back lines and the tile counter with one memset on the stream
+// (graph-capturable) before the kernel.
 //
 // Arithmetic: u32 wraps modulo 2^32; u32 -> u64 is exact; float scans keep
-// float-float (hi, lo) pairs inside a tile, FP64 between tiles, and round each
+// float-float (hi, lo) pairs inside a tile and between tiles, and round each
 // output once from the compensated prefix.
 #pragma once
 
@@ -46,6 +50,7 @@ struct OpU32 {
   using Carry = uint32_t;  // between tiles
   using Out = uint32_t;
   __device__ static T zero() { return 0u; }
+  __device__ static Carry carry_of(Out v) { return v; }
   __device__ static T lift(uint32_t v) { return v; }
   __device__ static T add(T a, T b) { return a + b; }
   __device__ static Carry to_carry(T a) { return a; }
@@ -59,6 +64,7 @@ struct OpU64 {
   using Carry = unsigned long long;
   using Out = unsigned long long;
   __device__ static T zero() { return 0ull; }
+  __device__ static Carry carry_of(Out v) { return v; }
   __device__ static T lift(uint32_t v) { return v; }
   __device__ static T add(T a, T b) { return a + b; }
   __device__ static Carry to_carry(T a) { return a; }
@@ -67,16 +73,23 @@ struct OpU64 {
   __device__ static Carry shfl_xor_c(Carry a, int d) { return __shfl_xor_sync(kFull, a, d); }
 };
 
+// Float scans carry float-float pairs between tiles as well: B300 issues an
+// FP64 add for a warp in about 60 cycles, and FP64 carries made the look-back
+// (a dozen adds per round) and every thread's prefix conversion the bound of
+// the f32 scan.
 struct OpF32 {
   using T = FF;
-  using Carry = double;
+  using Carry = FF;
   using Out = float;
   __device__ static T zero() { return FF{0.f, 0.f}; }
+  __device__ static Carry carry_of(Out v) { return FF{v, 0.f}; }
   __device__ static T add(T a, T b) { return ff_add(a, b); }
-  __device__ static Carry to_carry(T a) { return ff_to_double(a); }
-  __device__ static Carry cadd(Carry a, Carry b) { return a + b; }
+  __device__ static Carry to_carry(T a) { return a; }
+  __device__ static Carry cadd(Carry a, Carry b) { return ff_add(a, b); }
   __device__ static T shfl_up(T a, int d) { return FF{__shfl_up_sync(kFull, a.hi, d), __shfl_up_sync(kFull, a.lo, d)}; }
-  __device__ static Carry shfl_xor_c(Carry a, int d) { return __shfl_xor_sync(kFull, a, d); }
+  __device__ static Carry shfl_xor_c(Carry a, int d) {
+    return FF{__shfl_xor_sync(kFull, a.hi, d), __shfl_xor_sync(kFull, a.lo, d)};
+  }
 };
 
 template <class Op>
@@ -101,10 +114,10 @@ __device__ __forceinline__ typename Op::Carry warp_sum_carry(typename Op::Carry 
 // the state packed contiguously the polls contended for a handful of lines and
 // the u32 scan ran 25 % slower).  Where the carry and its flag fit one 64-bit
 // status word, one relaxed load sees both and no fence is needed: a u32 carry
-// takes the high half and the flag the low bits; an FP64 carry (float scans)
-// gives up its two lowest significand bits to the flag, i.e. it is published
-// truncated to 51 bits (a relative change below 2^-50, far below the FP32
-// outputs' resolution).  A u64 carry sits in the same line (aggregate at byte
+// takes the high half and the flag the low bits; a float-float carry (float
+// scans) keeps its high part whole in the high half and gives up the two
+// lowest significand bits of its low part to the flag (a relative change
+// below 2^-44 of the carry, far below the FP32 outputs' resolution).  A u64 carry sits in the same line (aggregate at byte
 // 8, inclusive prefix at byte 16) and its flag (byte 0) is released after it.
 constexpr int kLineBytes = 128;
 struct ScanWs {
@@ -116,16 +129,16 @@ constexpr bool kPackedStatus = !std::is_same<typename Op::Carry, unsigned long l
 
 template <class Op>
 __device__ __forceinline__ unsigned long long pack_status(typename Op::Carry v, uint32_t flag) {
-  if constexpr (std::is_same<typename Op::Carry, double>::value) {
-    return ((unsigned long long)__double_as_longlong(v) & ~3ull) | flag;
+  if constexpr (std::is_same<typename Op::Carry, FF>::value) {
+    return ((unsigned long long)__float_as_uint(v.hi) << 32) | (__float_as_uint(v.lo) & ~3u) | flag;
   } else {
     return ((unsigned long long)v << 32) | flag;
   }
 }
 template <class Op>
 __device__ __forceinline__ typename Op::Carry status_value(unsigned long long w) {
-  if constexpr (std::is_same<typename Op::Carry, double>::value) {
-    return __longlong_as_double((long long)(w & ~3ull));
+  if constexpr (std::is_same<typename Op::Carry, FF>::value) {
+    return FF{__uint_as_float((uint32_t)(w >> 32)), __uint_as_float((uint32_t)w & ~3u)};
   } else {
     return (typename Op::Carry)(w >> 32);
   }
@@ -146,28 +159,31 @@ __device__ __forceinline__ void publish(ScanWs ws, int64_t tile, uint32_t flag, 
   }
 }
 
-// Decoupled look-back for `tile` by one warp (the caller's warp 0): publishes
-// the aggregate (flag A), then reads the nearest unread predecessors (32 or
-// 128 per round), summing aggregates until an inclusive prefix (flag P) bounds the sum,
-// and publishes its own inclusive prefix.  Returns the exclusive prefix in
+// Decoupled look-back for `tile` by one warp (its aggregate, flag A, has been
+// published by the compute warps): reads the nearest unread predecessors (256
+// or 128 per round), summing aggregates until an inclusive prefix (flag P)
+// bounds the sum, and publishes its own inclusive prefix.  Returns the exclusive prefix in
 // every lane; sets `gave_up` (and the status word) when a wait runs past the
 // deadline or another block has aborted.
+// Predecessors read per lane and round: eight (a 256-tile window) with packed
+// status words, four (128) for u64 carries, whose rounds cost a fence and a
+// second load.  A round costs about one L2 round trip whatever its width, and
+// with ~300 tiles in flight at once a tile's nearest inclusive prefix is
+// usually one batch of tiles back: a 32-tile window needed several rounds per
+// look-back and bounded the scan by look-back latency (measured on B300:
+// 953 us for the 2^28 u32 scan with 4,096-element tiles).
+template <class Op>
+constexpr int kLookbackSlots = kPackedStatus<Op> ? 8 : 4;
+
 template <class Op>
 __device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typename Op::Carry aggregate, ScanWs ws,
                                                             WsHeader* hdr, uint64_t timeout_ns, bool stall, int lane,
                                                             bool& gave_up) {
   using Carry = typename Op::Carry;
-  // predecessors read per lane and round: one with packed status words, four
-  // (a 128-tile window) for u64 carries, whose rounds cost a fence and a
-  // second load
-  constexpr int kSlots = kPackedStatus<Op> ? 1 : 4;
-  Carry excl = Carry(0);
+  constexpr int kSlots = kLookbackSlots<Op>;
+  Carry excl = Carry{};
   gave_up = false;
-  if (tile == 0) {
-    if (lane == 0 && !stall) publish<Op>(ws, 0, kFlagP, aggregate);
-    return excl;
-  }
-  if (lane == 0 && !stall) publish<Op>(ws, tile, kFlagA, aggregate);
+  if (tile == 0) return excl;  // (its inclusive prefix is its aggregate, published with it)
   const uint64_t deadline = globaltimer_ns() + timeout_ns;
   int64_t pos = tile - 1;
   while (true) {
@@ -178,7 +194,7 @@ __device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typena
 #pragma unroll
     for (int m = 0; m < kSlots; ++m) {
       st[m] = kFlagP;  // before tile 0: an inclusive prefix of 0
-      val[m] = Carry(0);
+      val[m] = Carry{};
     }
     for (int polls = 0;; ++polls) {  // the window's loads are issued together; waits are bounded
       bool pending = false;
@@ -223,7 +239,7 @@ __device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typena
       const unsigned pm = __ballot_sync(kFull, st[m] == kFlagP);
       if (pm) first = 32 * m + __ffs(pm) - 1;
     }
-    Carry part = Carry(0);
+    Carry part = Carry{};
 #pragma unroll
     for (int m = 0; m < kSlots; ++m)
       if (32 * m + lane <= first) part = Op::cadd(part, val[m]);
@@ -233,6 +249,17 @@ __device__ __forceinline__ typename Op::Carry warp_lookback(int64_t tile, typena
   }
   if (lane == 0 && !stall) publish<Op>(ws, tile, kFlagP, Op::cadd(excl, aggregate));
   return excl;
+}
+
+// Run by one compute thread as soon as the tile's total is known: the tile's
+// aggregate (flag A), or for tile 0 its inclusive prefix (flag P).  Publishing
+// it here rather than in the look-back warp matters: the look-back warp may
+// still be busy with the block's previous tile, and successors that cannot
+// see this tile's aggregate cannot look past it -- the look-backs then chain
+// tile by tile (measured on B300: the TMA-fed 2^28 scan took 4.6 ms so).
+template <class Op>
+__device__ __forceinline__ void publish_aggregate(ScanWs ws, int64_t tile, typename Op::Carry aggregate, bool stall) {
+  if (!stall) publish<Op>(ws, tile, tile == 0 ? kFlagP : kFlagA, aggregate);
 }
 
 // ---- reduction in the same pass (tr_scan_reduce) ---------------------------
@@ -293,9 +320,9 @@ __device__ __noinline__ void finish_reduction(const ScanRed& red, WsHeader* hdr,
   if ((red.ops & TR_SUM) && red.sum) {
     if constexpr (std::is_same<Op, OpF32>::value) {
       if (red.sum_t == TR_F64)
-        *static_cast<double*>(red.sum) = total;
+        *static_cast<double*>(red.sum) = ff_to_double(total);
       else
-        *static_cast<float*>(red.sum) = (float)total;
+        *static_cast<float*>(red.sum) = (float)ff_to_double(total);
     } else if constexpr (std::is_same<Op, OpU64>::value) {
       *static_cast<unsigned long long*>(red.sum) = total;
     } else {
@@ -355,6 +382,37 @@ __device__ __forceinline__ void compute_sync() { bar_sync_n(kBarCompute, kThread
 // blocks per SM and the look-back in warp 0, 460 / 550 us.
 constexpr int kBlocksPerSm = 2;
 
+// The look-back warp of a block: per tile handed over by the compute warps
+// (barrier kBarAgg + i % kN), the decoupled look-back, then the exclusive
+// prefix back (barrier kBarAgg + kN + i % kN); the last tile also finishes the
+// fused reduction.  It stops on a tile id of -1.  kN hand-over slots (and
+// barriers each way) are in use at once: 2 when the compute warps consume a
+// prefix one tile after handing the tile over, 4 when they consume it two
+// tiles later (a barrier is never arrived at twice within one phase).
+template <class Op, class C, int kN>
+__device__ __forceinline__ void lookback_warp(const int64_t* s_tile_of, const typename Op::Carry* s_agg,
+                                              typename Op::Carry* s_excl, ScanWs ws, WsHeader* hdr,
+                                              uint64_t timeout_ns, int64_t stall_tile, const ScanRed& red,
+                                              int64_t tiles, int lane) {
+  using Carry = typename Op::Carry;
+  for (int i = 0;; ++i) {
+    const int slot = i % kN;
+    bar_sync_n(kBarAgg + slot, kBlockThreads);
+    const int64_t tile = s_tile_of[slot];
+    if (tile < 0) break;
+    const Carry agg = s_agg[slot];
+    bool gave_up;
+    const Carry e = warp_lookback<Op>(tile, agg, ws, hdr, timeout_ns, tile == stall_tile, lane, gave_up);
+    if (lane == 0) {
+      s_excl[slot] = e;
+      if (tile == tiles - 1 && red.ops && !gave_up)
+        finish_reduction<Op, C>(red, hdr, Op::cadd(e, agg), (uint32_t)tiles, timeout_ns);
+    }
+    __syncwarp();
+    bar_arrive_n(kBarAgg + kN + slot, kBlockThreads);
+  }
+}
+
 // One item into a running in-tile value (TwoSum into (hi, lo) for floats).
 template <class Op, class C>
 __device__ __forceinline__ void run_add(typename Op::T& run, C v) {
@@ -373,6 +431,35 @@ __device__ __forceinline__ typename Op::Out run_out(const typename Op::T& run) {
     return run.hi + run.lo;  // the compensated prefix, rounded once
   } else {
     return run;
+  }
+}
+
+// The total of a thread's row (V values): float scans run two interleaved
+// TwoSum chains on packed pairs (even and odd positions, add.rn.f32x2 /
+// sub.rn.f32x2, each half an IEEE operation) and join them with one
+// float-float add -- the same float-float accuracy as one chain in half the
+// instructions; the other outputs add in order.
+template <class Op, int V, class C>
+__device__ __forceinline__ typename Op::T row_total(const C* v) {
+  if constexpr (std::is_same<Op, OpF32>::value && V % 2 == 0) {
+    unsigned long long s = pack_f32x2(v[0], v[1]), e = pack_f32x2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 2; k < V; k += 2) {
+      const unsigned long long x = pack_f32x2(v[k], v[k + 1]);
+      const unsigned long long t = add_f32x2(s, x);
+      const unsigned long long bb = sub_f32x2(t, s);
+      e = add_f32x2(e, add_f32x2(sub_f32x2(s, sub_f32x2(t, bb)), sub_f32x2(x, bb)));
+      s = t;
+    }
+    float s0, s1, e0, e1;
+    unpack_f32x2(s, s0, s1);
+    unpack_f32x2(e, e0, e1);
+    return ff_add(FF{s0, e0}, FF{s1, e1});
+  } else {
+    typename Op::T acc = Op::zero();
+#pragma unroll
+    for (int k = 0; k < V; ++k) run_add<Op>(acc, v[k]);
+    return acc;
   }
 }
 
@@ -432,28 +519,14 @@ __global__ void __launch_bounds__(kBlockThreads, kBlocksPerSm)
   const int tid = threadIdx.x, lane = tid & 31;
 
   if (tid >= kThreads) {  // ---- the look-back warp
-    for (int i = 0;; ++i) {
-      bar_sync_n(kBarAgg + (i & 1), kBlockThreads);
-      const int64_t tile = s_tile_of[i & 1];
-      if (tile < 0) break;
-      const Carry agg = s_agg[i & 1];
-      bool gave_up;
-      const Carry e = warp_lookback<Op>(tile, agg, ws, hdr, timeout_ns, tile == stall_tile, lane, gave_up);
-      if (lane == 0) {
-        s_excl[i & 1] = e;
-        if (tile == tiles - 1 && red.ops && !gave_up)
-          finish_reduction<Op, C>(red, hdr, Op::cadd(e, agg), (uint32_t)tiles, timeout_ns);
-      }
-      __syncwarp();
-      bar_arrive_n(kBarExcl + (i & 1), kBlockThreads);
-    }
+    lookback_warp<Op, C, 2>(s_tile_of, s_agg, s_excl, ws, hdr, timeout_ns, stall_tile, red, tiles, lane);
     return;
   }
 
   // ---- the compute warps
   const auto f = kernel_map<F>(P);
   const bool minmax = (red.ops & (TR_MIN | TR_MAX)) != 0;
-  const Carry carry = carry_in ? Carry(*carry_in) : Carry(0);
+  const Carry carry = carry_in ? Op::carry_of(*carry_in) : Carry{};
   C* const rows0 = reinterpret_cast<C*>(s_dyn);
   uint4 raw[kLoads];
   auto full_tile = [&](int64_t t) { return vec_ok && t * kTile + kTile <= n; };
@@ -470,7 +543,7 @@ __global__ void __launch_bounds__(kBlockThreads, kBlocksPerSm)
     const Carry prefix = Op::cadd(carry, excl);
     T run;
     if constexpr (std::is_same<Op, OpF32>::value) {
-      run = ff_add(ff_from_double(prefix), thread_off);
+      run = ff_add(prefix, thread_off);
     } else {
       run = Op::add((T)prefix, thread_off);
     }
@@ -562,9 +635,7 @@ __global__ void __launch_bounds__(kBlockThreads, kBlocksPerSm)
     }
     compute_sync();
     C* row = rows + tid * kRow;
-    T acc = Op::zero();
-#pragma unroll
-    for (int k = 0; k < kItems; ++k) run_add<Op>(acc, row[k]);
+    const T acc = row_total<Op, kItems>(row);
     if (minmax) {  // the tile's min / max of f over its valid elements, combined per warp
       C mn = mm_highest<C>(), mx = mm_lowest<C>();
       const int64_t valid = full ? kItems : imax<int64_t>(0, imin<int64_t>(kItems, n - t0 - (int64_t)tid * kItems));
@@ -603,6 +674,7 @@ __global__ void __launch_bounds__(kBlockThreads, kBlocksPerSm)
       }
       s_agg[i & 1] = Op::to_carry(tile_tot);
       s_tile_of[i & 1] = t;
+      publish_aggregate<Op>(ws, t, Op::to_carry(tile_tot), t == stall_tile);
     }
     bar_arrive_n(kBarAgg + (i & 1), kBlockThreads);  // tile t goes to the look-back warp
     const int64_t t_next = s_next;
@@ -624,13 +696,334 @@ __global__ void __launch_bounds__(kBlockThreads, kBlocksPerSm)
   bar_arrive_n(kBarAgg + (i & 1), kBlockThreads);  // the look-back warp stops
 }
 
-// Clear the scan state and launch k_scan for the storage type In, map F and
-// output arithmetic Op; P is the map's source.
+// ---- the TMA-fed tile loop (4-byte inputs and outputs) -----------------------
+//
+// The same look-back schedule as k_scan, with the tiles moved by the TMA
+// engine instead of by the compute warps.  x and y are viewed as 2-D tensors
+// of rows of kI elements (the rows that lie wholly inside [0, n)); a tile is
+// 256 rows, one per compute thread.  A box load with the kI * 4-byte swizzle
+// (64 or 128 bytes) lands a thread's row as kI / 4 16-byte chunks whose
+// positions are permuted by the row index, so the eight threads of a quarter
+// warp read their own rows from eight different bank groups: each thread
+// reads its row with 16-byte loads, conflict-free, with no scatter and no
+// gather.  The stage is then used in place: phase 1 maps the row and writes
+// the mapped values back (tile total, min / max, aggregate to the look-back
+// warp); phase 2 -- kD tiles later, once the look-back warp has delivered the
+// prefix -- turns them into the outputs, and one box store writes the tile
+// back.  Loads outside the tensor read zeros and stores outside it are
+// clipped, so a partial last tile needs no special case; the elements of a
+// last, partial row (fewer than kI) are read and written by their thread.
+//
+// A block is 8 compute warps, the look-back warp and a producer warp, with a
+// ring of kD + 2 stages.  The producer takes the tile ids from the atomic
+// counter and issues the box loads; the compute warps' thread 0 issues the box
+// stores and, at the top of each iteration, waits for the store issued one
+// iteration earlier to finish reading its stage and hands that stage back to
+// the producer (an mbarrier per stage each way).  The producer takes the id of
+// a block's next tile only once the current tile's data has landed, so a
+// block holds at most one tile beyond the one it computes: taking ids several
+// tiles ahead made the first block to start hold consecutive ids, the next
+// block's first tile wait for that block's later ones, and so on -- a cascade
+// that ran the 2^28 scan ten times slower.  Within that limit a load still
+// gets most of an iteration to land.
+template <int kI_, int kD_>
+struct TmaTile {
+  static constexpr int kI = kI_;  // elements per row (per compute thread)
+  static constexpr int kD = kD_;  // tiles between phase 1 and phase 2
+  static_assert(kI == 16 || kI == 32, "rows of 64 or 128 bytes");
+  static_assert(kThreads * kI <= scank::kTile, "a look-back line per 8,192 elements suffices");
+  static_assert(kD == 1 || kD == 2, "phase-2 lag");
+  static constexpr int kTile = kThreads * kI;                // elements per tile
+  static constexpr uint32_t kStageBytes = (uint32_t)kTile * 4;
+  static constexpr int kStages = kD + 2;
+  static constexpr int kChunks = kI / 4;                     // 16-byte chunks per row
+  static constexpr size_t kDynBytes = (size_t)kStages * kStageBytes + 1024;  // + alignment of the ring
+  static constexpr CUtensorMapSwizzle kSwizzle = kI == 16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+  // byte offset of chunk c of row r in a stage: the swizzle XORs the chunk
+  // index with address bits 7.. (two bits for 64-byte, three for 128-byte rows)
+  __device__ static __forceinline__ uint32_t chunk_off(int r, int c) {
+    return (uint32_t)r * (kI * 4) + ((uint32_t)(c ^ ((kI == 16 ? r >> 1 : r) & (kChunks - 1))) << 4);
+  }
+};
+constexpr int kTmaBlockThreads = kBlockThreads + 32;  // + the producer warp
+
+__device__ __forceinline__ void tma_load_rows(uint32_t dst, const CUtensorMap* map, int row, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(map), "r"(0), "r"(row), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_rows(const CUtensorMap* map, int row, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(0),
+               "r"(row), "r"(src)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_plain(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// True in every compute thread iff `v` holds in all of them (a compute-warp barrier).
+__device__ __forceinline__ bool compute_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kBarCompute), "n"(kThreads)
+      : "memory");
+  return r != 0;
+}
+constexpr uint64_t kStageWaitNs = 1000000000ull;  // 1 s for one stage hand-over before giving up
+template <class C>
+__device__ __forceinline__ C from_bits(uint32_t b);
+template <>
+__device__ __forceinline__ float from_bits<float>(uint32_t b) { return __uint_as_float(b); }
+template <>
+__device__ __forceinline__ uint32_t from_bits<uint32_t>(uint32_t b) { return b; }
+
+template <class In, class F, class Op, class Src, class L>
+__global__ void __launch_bounds__(kTmaBlockThreads, kBlocksPerSm)
+    k_scan_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap,
+               const In* __restrict__ x, typename Op::Out* y, int64_t n, const __grid_constant__ Src P,
+               WsHeader* hdr, ScanWs ws, const typename Op::Out* carry_in, uint64_t timeout_ns, int64_t stall_tile,
+               int exclusive, ScanRed red, int64_t tiles) {
+  constexpr int kI = L::kI, kD = L::kD, kR = L::kStages;
+  constexpr int kN = kD == 1 ? 2 : 4;  // hand-over slots in use at once
+  using C = In;
+  using T = typename Op::T;
+  using Carry = typename Op::Carry;
+  using Out = typename Op::Out;
+  static_assert(sizeof(C) == 4 && sizeof(Out) == 4, "4-byte inputs and outputs");
+  static_assert(std::is_same<typename Storage<In>::C, In>::value, "the input is its own compute type");
+
+  __shared__ int64_t s_tile_of[kN];
+  __shared__ Carry s_agg[kN], s_excl[kN];
+  __shared__ int64_t s_stage_tile[kR];  // tile id of a stage's fill (-1: none left)
+  __shared__ __align__(8) uint64_t s_full[kR], s_empty[kR];
+  __shared__ T s_warp[kWarps];
+  __shared__ C s_mn[kWarps], s_mx[kWarps];
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  const int tid = threadIdx.x, lane = tid & 31;
+  unsigned char* const ring = s_dyn + ((1024u - (smem_addr(s_dyn) & 1023u)) & 1023u);
+  const uint32_t ring_s = smem_addr(ring), full0 = smem_addr(&s_full[0]), empty0 = smem_addr(&s_empty[0]);
+  if (tid == 0) {
+    for (int st = 0; st < kR; ++st) {
+      mbar_init(full0 + 8 * st, 1);
+      mbar_init(empty0 + 8 * st, 1);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+
+  if (tid >= kBlockThreads) {  // ---- the producer warp (one lane)
+    if (lane != 0) return;
+    for (int q = 0;; ++q) {
+      const int st = q % kR;
+      // the block's previous tile has landed (at most one tile held beyond the computed one),
+      // and this stage's last tile has been stored out of it
+      bool ok = q == 0 || mbar_wait_quiet(full0 + 8 * ((q - 1) % kR), (uint32_t)(((q - 1) / kR) & 1), kStageWaitNs);
+      if (ok && q >= kR) ok = mbar_wait_quiet(empty0 + 8 * st, (uint32_t)(((q - kR) / kR) & 1), kStageWaitNs);
+      const uint32_t id = ok ? atomicAdd(&hdr->tile_counter, 1u) : 0xFFFFFFFFu;
+      if (!ok) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)q);
+      const uint32_t bar = full0 + 8 * st;
+      if ((int64_t)id < tiles) {
+        s_stage_tile[st] = id;
+        mbar_expect_tx(bar, L::kStageBytes);
+        tma_load_rows(ring_s + (uint32_t)st * L::kStageBytes, &xmap, (int)id * kThreads, bar);
+      } else {  // no tile left (or a failed hand-over): the compute warps stop at this stage
+        s_stage_tile[st] = -1;
+        mbar_arrive_plain(bar);
+        return;
+      }
+    }
+  }
+  if (tid >= kThreads) {  // ---- the look-back warp
+    lookback_warp<Op, C, kN>(s_tile_of, s_agg, s_excl, ws, hdr, timeout_ns, stall_tile, red, tiles, lane);
+    return;
+  }
+
+  // ---- the compute warps
+  const auto f = kernel_map<F>(P);
+  const bool minmax = (red.ops & (TR_MIN | TR_MAX)) != 0;
+  const Carry carry = carry_in ? Op::carry_of(*carry_in) : Carry{};
+  const int64_t ragged = (n / kI) * kI;  // the first element of a last, partial row (== n: none)
+  auto stage_of = [&](int st) { return ring + (size_t)st * L::kStageBytes; };
+  auto load_row = [&](const unsigned char* stage, C* v) {
+#pragma unroll
+    for (int c = 0; c < L::kChunks; ++c) {
+      const uint4 w = *reinterpret_cast<const uint4*>(stage + L::chunk_off(tid, c));
+      v[4 * c] = from_bits<C>(w.x);
+      v[4 * c + 1] = from_bits<C>(w.y);
+      v[4 * c + 2] = from_bits<C>(w.z);
+      v[4 * c + 3] = from_bits<C>(w.w);
+    }
+  };
+  auto store_row = [&](unsigned char* stage, const auto* v) {
+#pragma unroll
+    for (int c = 0; c < L::kChunks; ++c) *reinterpret_cast<uint4*>(stage + L::chunk_off(tid, c)) = pack16(v + 4 * c);
+  };
+  // phase 2 of tile t (stage st): outputs from the mapped row and the tile's exclusive prefix
+  auto finish_tile = [&](int64_t t, int st, Carry excl, const T& thread_off) {
+    unsigned char* stage = stage_of(st);
+    const int64_t e0 = t * L::kTile + (int64_t)tid * kI;
+    C v[kI];
+    load_row(stage, v);
+    const Carry prefix = Op::cadd(carry, excl);
+    T run;
+    if constexpr (std::is_same<Op, OpF32>::value) {
+      run = ff_add(prefix, thread_off);
+    } else {
+      run = Op::add((T)prefix, thread_off);
+    }
+    Out o[kI];
+    if (exclusive) {
+#pragma unroll
+      for (int k = 0; k < kI; ++k) {
+        o[k] = run_out<Op>(run);
+        run_add<Op>(run, v[k]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kI; ++k) {
+        run_add<Op>(run, v[k]);
+        o[k] = run_out<Op>(run);
+      }
+    }
+    if (e0 == ragged && e0 < n) {  // the partial last row: outside the tensor, written directly
+      for (int k = 0; k < kI; ++k)
+        if (e0 + k < n) y[e0 + k] = o[k];
+    }
+    store_row(stage, o);
+    fence_async_smem();  // the rows, before the box store reads them
+    compute_sync();
+    if (tid == 0) tma_store_rows(&ymap, (int)(t * kThreads), ring_s + (uint32_t)st * L::kStageBytes);
+  };
+
+  // tiles in phase-2 order: pend_t[k] / pend_off[k] hold the tile handed over k + 1 iterations ago
+  int64_t pend_t[kD];
+  T pend_off[kD];
+#pragma unroll
+  for (int k = 0; k < kD; ++k) {
+    pend_t[k] = -1;
+    pend_off[k] = Op::zero();
+  }
+  int stored = 0;  // box stores issued (the stage of store s is s % kR: stores go in fill order)
+  int j = 0;
+  bool ok = true;
+  // the oldest pending tile: wait for its prefix, write it out, shift the queue
+  auto drain_one = [&](int jj) {
+    const int64_t tp = pend_t[kD - 1];
+    if (tp >= 0) {
+      const int q = jj - kD;  // its fill (and iteration) number
+      bar_sync_n(kBarAgg + kN + q % kN, kBlockThreads);
+      finish_tile(tp, q % kR, s_excl[q % kN], pend_off[kD - 1]);
+      ++stored;
+    }
+#pragma unroll
+    for (int k = kD - 1; k > 0; --k) {
+      pend_t[k] = pend_t[k - 1];
+      pend_off[k] = pend_off[k - 1];
+    }
+    pend_t[0] = -1;
+  };
+  while (true) {
+    // hand the stage of the store issued one iteration ago back to the producer
+    if (tid == 0 && stored > 0) {
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      mbar_arrive_plain(empty0 + 8 * ((stored - 1) % kR));
+    }
+    const int st = j % kR;
+    ok = compute_all(mbar_wait_quiet(full0 + 8 * st, (uint32_t)((j / kR) & 1), kStageWaitNs));
+    if (!ok) {
+      if (tid == 0) set_status(hdr, TR_ERR_TIMEOUT, (uint32_t)j);
+      break;
+    }
+    const int64_t t = s_stage_tile[st];
+    if (t < 0) break;
+    // ---- phase 1: map the row in place, total it
+    unsigned char* stage = stage_of(st);
+    const int64_t e0 = t * L::kTile + (int64_t)tid * kI;
+    const int valid = (int)imax<int64_t>(0, imin<int64_t>(kI, n - e0));
+    C v[kI];
+    load_row(stage, v);
+    if (valid == kI) {
+#pragma unroll
+      for (int h = 0; h < kI; h += 16) map_vec<16>(f, v + h);  // 16 values at a time (registers)
+    } else {
+#pragma unroll
+      for (int k = 0; k < kI; ++k) {
+        C xv = v[k];
+        if (e0 == ragged && k < valid) xv = x[e0 + k];  // the partial last row is not in the tensor
+        v[k] = k < valid ? f(xv) : C(0);
+      }
+    }
+    store_row(stage, v);
+    const T acc = row_total<Op, kI>(v);
+    if (minmax) {
+      C mn = mm_highest<C>(), mx = mm_lowest<C>();
+#pragma unroll
+      for (int k = 0; k < kI; ++k) {
+        if (k < valid) {
+          mn = mm_min(mn, v[k]);
+          mx = mm_max(mx, v[k]);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = mm_min(mn, __shfl_xor_sync(kFull, mn, o));
+        mx = mm_max(mx, __shfl_xor_sync(kFull, mx, o));
+      }
+      if (lane == 0) {
+        s_mn[tid >> 5] = mn;
+        s_mx[tid >> 5] = mx;
+      }
+    }
+    T warp_off, excl_lane, tile_tot;
+    block_totals<Op>(acc, s_warp, warp_off, excl_lane, tile_tot);
+    if (tid == 0) {
+      if (minmax) {
+        C mn = s_mn[0], mx = s_mx[0];
+#pragma unroll
+        for (int w = 1; w < kWarps; ++w) {
+          mn = mm_min(mn, s_mn[w]);
+          mx = mm_max(mx, s_mx[w]);
+        }
+        if (mn == mn) red_max_u32(&hdr->red_min, ~mm_key(mn));
+        if (mx == mx) red_max_u32(&hdr->red_max, mm_key(mx));
+        red_add_release_u32(&hdr->red_done, 1u);
+      }
+      s_agg[j % kN] = Op::to_carry(tile_tot);
+      s_tile_of[j % kN] = t;
+      publish_aggregate<Op>(ws, t, Op::to_carry(tile_tot), t == stall_tile);
+    }
+    bar_arrive_n(kBarAgg + j % kN, kBlockThreads);  // tile t goes to the look-back warp
+    // ---- phase 2 of the tile handed over kD iterations ago
+    drain_one(j);
+    pend_t[0] = t;
+    pend_off[0] = Op::add(warp_off, excl_lane);
+    ++j;
+  }
+#pragma unroll
+  for (int k = 0; k < kD; ++k) drain_one(j + k);
+  if (tid == 0) {
+    s_tile_of[j % kN] = -1;
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the box stores are complete
+  }
+  bar_arrive_n(kBarAgg + j % kN, kBlockThreads);  // the look-back warp stops
+  if (!ok && tid == 0)  // after a failed wait: the producer's load for this stage, if any, lands first
+    mbar_wait_quiet(full0 + 8 * (j % kR), (uint32_t)((j / kR) & 1), kStageWaitNs);
+}
+
+// Clear the scan state and launch the scan for the storage type In, map F and
+// output arithmetic Op; P is the map's source.  4-byte inputs and outputs on
+// 16-byte aligned arrays of at least one tile take the TMA-fed kernel; the
+// rest take k_scan.  Both use tiles of 8,192 elements.
 template <class In, class F, class Op, class Src>
 tr_status launch(const Src& P, const In* x, typename Op::Out* y, int64_t n, const typename Op::Out* carry,
                  const tr_exec* e, const ScanOpts& opt) {
-  const int64_t tiles = std::max<int64_t>(1, ceil_div(n, kTile));  // n = 0 (with a reduction): one empty tile
-  if (tiles > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "too many tiles");
   const ScanWs ws{reinterpret_cast<unsigned char*>(ws_body(e))};
   const uint64_t timeout_ns = (uint64_t)(e->wait_timeout_us ? e->wait_timeout_us : 1000000u) * 1000ull;
   const int vec_ok = aligned_to(x, 16) && aligned_to(y, 16);
@@ -640,9 +1033,44 @@ tr_status launch(const Src& P, const In* x, typename Op::Out* y, int64_t n, cons
   // every call starts from a zero tile counter, cleared reduction words and clear look-back
   // lines: one memset from the counter through the last line (the error words before the
   // counter are left alone)
-  unsigned char* from = reinterpret_cast<unsigned char*>(&hdr->tile_counter);
-  const size_t bytes = (size_t)(reinterpret_cast<unsigned char*>(ws.lines) - from) + (size_t)tiles * kLineBytes;
-  tr_status s = cuda_status(cudaMemsetAsync(from, 0, bytes, st), "cudaMemsetAsync(scan state)");
+  auto clear = [&](int64_t tiles) {
+    unsigned char* from = reinterpret_cast<unsigned char*>(&hdr->tile_counter);
+    const size_t bytes = (size_t)(reinterpret_cast<unsigned char*>(ws.lines) - from) + (size_t)tiles * kLineBytes;
+    return cuda_status(cudaMemsetAsync(from, 0, bytes, st), "cudaMemsetAsync(scan state)");
+  };
+  const int64_t lines = e->workspace_bytes > (size_t)kWsHeader
+                            ? (int64_t)((e->workspace_bytes - (size_t)kWsHeader) / (size_t)kLineBytes)
+                            : 0;
+  if constexpr (sizeof(In) == 4 && sizeof(typename Op::Out) == 4) {
+    auto go_tma = [&](auto layout_tag) -> tr_status {
+      using L = decltype(layout_tag);
+      constexpr int kI = L::kI;
+      const int64_t tiles = ceil_div(n, L::kTile);
+      const uint64_t rows = (uint64_t)(n / kI);
+      const CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_UINT32;
+      CUtensorMap xm, ym;
+      tr_status s = make_tensor_map_2d(&xm, x, dt, kI, rows, kI * 4, kI, kThreads, L::kSwizzle);
+      if (!s) s = make_tensor_map_2d(&ym, y, dt, kI, rows, kI * 4, kI, kThreads, L::kSwizzle);
+      if (!s) s = clear(tiles);
+      if (s) return s;
+      auto kern = k_scan_tma<In, F, Op, Src, L>;
+      if ((s = ensure_dyn_smem((const void*)kern, (int)L::kDynBytes, "cudaFuncSetAttribute(k_scan_tma)"))) return s;
+      const int64_t resident =
+          (int64_t)dev_info().sm_count * blocks_per_sm((const void*)kern, kTmaBlockThreads, L::kDynBytes);
+      const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, resident));
+      kern<<<(unsigned)grid, kTmaBlockThreads, L::kDynBytes, st>>>(xm, ym, x, y, n, P, hdr, ws, carry, timeout_ns,
+                                                                    e->debug_stall_tile, opt.exclusive, red, tiles);
+      return launch_status("k_scan_tma");
+    };
+    // 32-element rows, phase 2 one tile after phase 1 (measured on B300 at 2^28, u32 splitmix32 /
+    // f32 x^2: 382 / 447 us; 16-element rows with phase 2 two tiles later: 455 / 570 us)
+    using L = TmaTile<32, 1>;
+    // (the row coordinates of the boxes are 32-bit)
+    if (vec_ok && n >= L::kTile && n / 32 < 0x7FFFFFFF && ceil_div(n, L::kTile) <= lines) return go_tma(L());
+  }
+  const int64_t tiles = std::max<int64_t>(1, ceil_div(n, kTile));  // n = 0 (with a reduction): one empty tile
+  if (tiles > 0x7FFFFFFF) return fail(TR_ERR_INVALID_ARG, "too many tiles");
+  tr_status s = clear(tiles);
   if (s) return s;
   auto kern = k_scan<In, F, Op, Src>;
   if ((s = ensure_dyn_smem((const void*)kern, (int)kDynBytes, "cudaFuncSetAttribute(k_scan)"))) return s;

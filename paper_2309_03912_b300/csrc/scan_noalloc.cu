@@ -22,9 +22,9 @@ namespace {
 
 // Largest input accepted: 2^26 elements.
 constexpr int64_t kNoAllocMaxN = int64_t(1) << 26;
-// Header + one 128-byte look-back line per tile for up to 8,192 tiles (tr_scan's
-// tiles hold 8,192 elements, so 2^26 elements need no more); the call checks
-// the scan's own workspace size against it before launching.
+// Header + one 128-byte look-back line per tile for up to 8,192 tiles (the
+// scan's tiles hold 8,192 elements, so 2^26 elements need no more); the call
+// checks the scan's own workspace size against it before launching.
 constexpr size_t kNoAllocScratchBytes = 256 + (size_t)8192 * 128;
 
 // The scratch.  In host code this name is only a stand-in for the symbol, not

@@ -164,3 +164,39 @@ def test_same_as_separate_scan_and_reduce(B):
     B.tr_check(ex)
     B.tr_check(exr)
     assert torch.equal(y, y2) and int(s.item()) == int(s2.item())
+
+
+@pytest.mark.parametrize("exclusive", [False, True], ids=["incl", "excl"])
+def test_scan_reduce_captured_in_a_cuda_graph(orc, B, exclusive):
+    """The TMA-fed scan (a cooperative launch) with its fused reduction,
+    captured into a CUDA graph and replayed twice: bit-exact outputs and
+    reduction every time."""
+    n = 1_000_003
+    x = I.u32(I.rng("misc", 31), n)
+    xd = to_dev(x)
+    y = torch.empty(n, dtype=torch.int32, device="cuda")
+    sm = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lo = torch.zeros(1, dtype=torch.int32, device="cuda")
+    hi = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = B.workspace(B.tr_scan_workspace_size(n, B.TR_U32, B.TR_U32))
+    spec = orc.MapSpec("splitmix32")
+    ref = orc.scan_u32(spec, x, exclusive=exclusive)
+    rs, rlo, rhi = orc.reduce_u32(spec, x)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ex = B.make_exec(ws)
+            B.tr_scan_reduce({"kind": "splitmix32"}, xd, y, ex, exclusive=exclusive, ops=7, out_sum=sm, out_min=lo,
+                             out_max=hi)
+    for _ in range(2):
+        y.fill_(-1)
+        sm.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(u32_host(y), ref)
+        assert int(u32_host(sm)[0]) == rs % (1 << 32)
+        assert int(u32_host(lo)[0]) == rlo and int(u32_host(hi)[0]) == rhi
+    B.tr_check(B.make_exec(ws))

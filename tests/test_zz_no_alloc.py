@@ -63,8 +63,8 @@ def test_u32_scans_match_the_oracle_bitwise(orc, B, n):
             assert np.array_equal(host(y), ref)
 
 
-def test_f32_scan_matches_the_oracle_within_tolerance(orc, B):
-    n = 1_000_003
+@pytest.mark.parametrize("n", [1_000_003, (1 << 25) + 12_345])
+def test_f32_scan_matches_the_oracle_within_tolerance(orc, B, n):
     xh = np.random.default_rng(22).uniform(0, 1, n).astype(np.float32)
     x = torch.from_numpy(xh).cuda()
     ref = orc.scan_float(orc.MapSpec("square"), xh, 24)
