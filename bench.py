@@ -63,6 +63,7 @@ def parse():
                                               "(scan_u32, scan_f32, reduce_f64, mixers_2^20, batched, vandermonde, f16); "
                                               "skips the headline")
     p.add_argument("--config-log2", type=int, default=28, help="log2 size of the 2^28 scan configurations")
+    p.add_argument("--f16-log2", type=int, default=30, help="log2 size of the FP16-storage configuration")
     p.add_argument("--vander-log2-m", type=int, default=20,
                    help="log2 of the points of the Vandermonde configuration (smaller only for profiler captures)")
     p.add_argument("--head-n", type=int, default=N_HEAD,
@@ -480,7 +481,7 @@ def other_configs(args, stream, hbm_peak, tensor_peak=1781.3):
 
     if want('f16'):
         # FP16 storage, FP32 compute: Horner deg 8 sum/min/max, N = 2^30
-        xh, m = I.horner_f16(1 << 30)
+        xh, m = I.horner_f16(1 << args.f16_log2)
         xhd = torch.from_numpy(xh).cuda()
         ws = B.workspace(B.tr_reduce_workspace_size(xhd.numel(), B.TR_F16))
         ex = B.make_exec(ws, stream=stream)
@@ -488,7 +489,7 @@ def other_configs(args, stream, hbm_peak, tensor_peak=1781.3):
         mm = torch.empty(2, dtype=torch.float32, device="cuda")
         ms16, _, _ = time_launches(lambda: B.tr_reduce(m, xhd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
         got16 = (float(s.item()), float(mm[0].item()), float(mm[1].item()))
-        name16 = "reduce_f16_storage_horner8_2^30"
+        name16 = f"reduce_f16_storage_horner8_2^{args.f16_log2}"
         record(name16, ms16, xhd.numel(), xhd.numel() * 2, 1)
         # the same values in f32 storage: the plain FP32 comparison for the mixed-precision form
         xfd = xhd.float()
@@ -497,7 +498,7 @@ def other_configs(args, stream, hbm_peak, tensor_peak=1781.3):
         ex = B.make_exec(ws, stream=stream)
         ms32, _, _ = time_launches(lambda: B.tr_reduce(m, xfd, 7, s, mm[0:1], mm[1:2], ex), steps, warm, stream)
         got32 = (float(s.item()), float(mm[0].item()), float(mm[1].item()))
-        name32 = "reduce_f32_storage_horner8_2^30"
+        name32 = f"reduce_f32_storage_horner8_2^{args.f16_log2}"
         record(name32, ms32, xfd.numel(), xfd.numel() * 4, 1, {"f16_storage_speedup": round(ms32 / ms16, 3)})
         checks[name16] = {"kind": "reduce_f32c", "x": xh, "map": m, "got": got16}
         checks[name32] = {"kind": "reduce_f32c", "x": xh, "map": m, "got": got32, "same_values_as": name16}
