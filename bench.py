@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--no-configs", action="store_true", help="headline only")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     p.add_argument("--only", default="", help="comma-separated names of the extra configurations to run "
-                                              "(scan_u32, scan_f32, reduce_f64, mixers_2^20, batched, vandermonde, f16); "
+                                              "(scan_u32, scan_f32, rational_reduce, reduce_f64, mixers_2^20, batched, vandermonde, f16); "
                                               "skips the headline")
     p.add_argument("--config-log2", type=int, default=28, help="log2 size of the 2^28 scan configurations")
     p.add_argument("--f16-log2", type=int, default=30, help="log2 size of the FP16-storage configuration")
@@ -368,7 +368,36 @@ def other_configs(args, stream, hbm_peak, tensor_peak=1781.3):
         name = f"scan_u32_splitmix32_2^{args.config_log2}"
         record(name, ms, xud.numel(), xud.numel() * 8, 1)
         checks[name] = {"kind": "scan_u32", "x": xu, "got": y.cpu().numpy().view(np.uint32)}
+        # the same scan with sum / min / max of f from the same pass (one read of x, one write of y)
+        sr = torch.zeros(3, dtype=torch.int32, device="cuda")
+        ms_f, _, _ = time_launches(lambda: B.tr_scan_reduce({"kind": "splitmix32"}, xud, y, exs, ops=7,
+                                                            out_sum=sr[0:1], out_min=sr[1:2], out_max=sr[2:3]),
+                                   steps, warm, stream)
+        B.tr_check(exs)
+        name_f = f"scan_reduce_u32_splitmix32_2^{args.config_log2}"
+        record(name_f, ms_f, xud.numel(), xud.numel() * 8, 1,
+               {"fused": "inclusive scan + sum (mod 2^32) / min / max of f in one pass", "plain_scan_ms": round(ms, 5)})
+        checks[name_f] = {"kind": "scan_reduce_u32", "x": xu, "got": y.cpu().numpy().view(np.uint32),
+                          "red": sr.cpu().numpy().view(np.uint32).copy()}
         del xud, y
+
+    if want('rational_reduce'):
+        # the headline's map and inputs without segments: one sum / min / max over all 2^28 values (the
+        # map's own ceiling for the segmented step)
+        xr, mr, _ = I.rational_segments(N_HEAD, NSEG_HEAD)
+        xrd = torch.from_numpy(xr).cuda()
+        wsr = B.workspace(B.tr_reduce_workspace_size(xrd.numel(), B.TR_F32))
+        exr = B.make_exec(wsr, stream=stream)
+        sr = torch.empty(1, dtype=torch.float64, device="cuda")
+        mmr = torch.empty(2, dtype=torch.float32, device="cuda")
+        ms, _, _ = time_launches(lambda: B.tr_reduce(mr, xrd, 7, sr, mmr[0:1], mmr[1:2], exr), steps, warm, stream)
+        B.tr_check(exr)
+        name = "reduce_rational66_2^28_no_segments"
+        record(name, ms, xrd.numel(), xrd.numel() * 4, 1,
+               {"note": "the headline's map and input as one array: the cost of the map and the sum alone"})
+        checks[name] = {"kind": "reduce_rational", "x": xr, "map": mr,
+                        "got": (float(sr.item()), float(mmr[0].item()), float(mmr[1].item()))}
+        del xrd
 
     if want('scan_f32'):
         # f32 compensated scan of x^2, N = 2^28
@@ -407,14 +436,45 @@ def other_configs(args, stream, hbm_peak, tensor_peak=1781.3):
         kinds = {}
         for m in maps:
             kinds[m["kind"]] = kinds.get(m["kind"], 0) + 1
-        name = "batched_10000_arrays_mixed_maps"
-        record(name, ms_b, total, total * 4, 1,
-               {"plan": plan.describe(), "arrays": nb, "maps": kinds, "unbatched_eager_ms": round(ms_eager, 4),
-                "unbatched_graph_ms": round(ms_graph, 4), "speedup_vs_eager": round(ms_eager / ms_b, 2),
-                "speedup_vs_graph": round(ms_graph / ms_b, 2), "launches_unbatched": nb})
-        checks[name] = {"kind": "batched", "xs": xs, "maps": maps, "got": got}
+        plan_desc = plan.describe()
         plan.close()
         del dev
+        # the mix's roofline: the larger of the HBM time of its bytes and the FMA-pipe time of its
+        # arithmetic, counted per element from each map's operation sequence (FP32 lane operations on
+        # the FMA pipe: Horner degree d: d fmas + 1 for the compensated sum; rational dp/dq: dp + dq
+        # fmas + 6 for the correctly rounded quotient + 1; Newton, I steps: 11 I + 1), and of its
+        # reciprocals on the XU pipe (one per quotient)
+        props = torch.cuda.get_device_properties(0)
+        clock_hz = 2.032e9
+        fma_ops, xu_ops, per_map = 0.0, 0.0, {}
+        for m, L in zip(maps, lens):
+            if m["kind"] == "horner":
+                f_, x_, label = len(m["cp"]) - 1 + 1, 0, "horner"
+            elif m["kind"] == "rational":
+                f_, x_, label = (len(m["cp"]) - 1) + (len(m["cq"]) - 1) + 7, 1, "rational"
+            else:
+                f_, x_, label = 11 * m["iters"] + 1, m["iters"], "newton_cbrt"
+            fma_ops += f_ * int(L)
+            xu_ops += x_ * int(L)
+            d = per_map.setdefault(label, {"elements": 0, "fma_lane_ops": 0})
+            d["elements"] += int(L)
+            d["fma_lane_ops"] += f_ * int(L)
+        t_hbm = total * 4 / (hbm_peak * 1e9) * 1e3
+        t_fma = fma_ops / (props.multi_processor_count * 128 * clock_hz) * 1e3
+        t_xu = xu_ops / (props.multi_processor_count * 16 * clock_hz) * 1e3
+        floor_ms = max(t_hbm, t_fma, t_xu)
+        bound = {t_hbm: "hbm", t_fma: "fma pipe", t_xu: "xu pipe"}[floor_ms]
+        name = "batched_10000_arrays_mixed_maps"
+        record(name, ms_b, total, total * 4, 1,
+               {"plan": plan_desc, "arrays": nb, "maps": kinds, "unbatched_eager_ms": round(ms_eager, 4),
+                "unbatched_graph_ms": round(ms_graph, 4), "speedup_vs_eager": round(ms_eager / ms_b, 2),
+                "speedup_vs_graph": round(ms_graph / ms_b, 2), "launches_unbatched": nb,
+                "roofline": {"bound": bound, "floor_ms": round(floor_ms, 4), "frac": round(floor_ms / ms_b, 4),
+                             "hbm_ms": round(t_hbm, 4), "fma_pipe_ms": round(t_fma, 4), "xu_pipe_ms": round(t_xu, 4),
+                             "per_map": per_map,
+                             "peaks": f"measured HBM {hbm_peak} GB/s; FMA pipe {props.multi_processor_count} SMs x "
+                                      f"128 lanes x {clock_hz / 1e9} GHz; XU 16 lanes per SM"}})
+        checks[name] = {"kind": "batched", "xs": xs, "maps": maps, "got": got}
 
     if want('vandermonde'):
         # 4096 polynomials of degree 31 at 2^20 points: Y = V(x) C (16 GiB of FP32 output), split-BF16 on
@@ -562,6 +622,21 @@ def check_configs(checks, threads):
             bad = int(np.count_nonzero(c["got"] != oracle.scan_u32(oracle.MapSpec("splitmix32"), c["x"])))
             errs[name] = {"mismatches": bad, "bar": 0, "pass": bad == 0,
                           "checked": f"all {c['x'].size} outputs, bit for bit"}
+        elif k == "scan_reduce_u32":
+            spec = oracle.MapSpec("splitmix32")
+            rs, rlo, rhi = oracle.reduce_u32(spec, c["x"])
+            bad = int(np.count_nonzero(c["got"] != oracle.scan_u32(spec, c["x"])))
+            red_ok = [int(v) for v in c["red"]] == [rs % (1 << 32), rlo, rhi]
+            errs[name] = {"mismatches": bad + (0 if red_ok else 1), "bar": 0, "pass": bad == 0 and red_ok,
+                          "checked": f"all {c['x'].size} outputs and the sum, min, max, bit for bit"}
+        elif k == "reduce_rational":
+            m = c["map"]
+            spec = oracle.MapSpec(m["kind"], m["cp"], m["cq"])
+            rs, rlo, rhi, ra = oracle.reduce_float_mt(spec, c["x"], threads)
+            s, lo, hi = c["got"]
+            em = _minmax_rel(lo, hi, rlo, rhi)
+            errs[name] = _err(abs(s - rs) / ra, 1e-6, "the whole sum, min and max", em <= 1e-5,
+                              minmax_rel_max_abs=em, minmax_bar=1e-5)
         elif k == "scan_f32":
             ref = oracle.scan_float_sampled(oracle.MapSpec("square"), c["x"], c["pos"])
             e = _normwise(c["got"], ref, np.abs(ref))
@@ -711,7 +786,12 @@ def main():
     stream = torch.cuda.Stream()
 
     if args.only:
-        recs, _ = other_configs(args, stream, hbm_peak, tensor_peak)
+        recs, checks = other_configs(args, stream, hbm_peak, tensor_peak)
+        if not args.no_cpu:
+            import oracle
+            oracle.build()
+            for name, e in check_configs(checks, oracle.host_threads()).items():
+                recs[name]["error"] = e
         print(json.dumps({"configs": recs}))
         return 0
     h = headline(args, rank, world, stream)
