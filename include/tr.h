@@ -211,8 +211,8 @@ tr_status tr_scan_workspace_size(int64_t n, tr_dtype xt, tr_dtype yt, size_t* by
  * look-back", NVIDIA NVR-2016-002).  Supported (xt -> yt):
  *   U32 -> U32  modulo 2^32 (bit exact)
  *   U32 -> U64  exact
- *   F16/BF16/F32 -> F32  float-float within a tile, FP64 between tiles, each
- *                 output rounded once from the compensated prefix.
+ *   F16/BF16/F32 -> F32  float-float within and between tiles, each output
+ *                 rounded once from the compensated prefix.
  * d_carry_in (nullable, device, one element of yt's type) is added to every
  * output.  y may equal x when the element sizes match.  4-byte inputs and
  * outputs on 16-byte aligned arrays move through the TMA engine; the
@@ -235,14 +235,14 @@ enum { TR_SCAN_INCLUSIVE = 0, TR_SCAN_EXCLUSIVE = 1 };
  * Results of the reduction (device memory, one element each) do not include
  * the carry-in:
  *   U32 -> U32:   sum_t U32 (modulo 2^32);  U32 -> U64: sum_t U64 (exact);
- *   float scans:  sum_t F64 (the scan's FP64 total of the tiles' compensated
- *                 sums) or F32;  min / max: F32 for float input, U32 for u32,
- *                 ignoring NaN; for n = 0 the identities.
+ *   float scans:  sum_t F64 (the scan's float-float total of the tiles'
+ *                 compensated sums, rounded once) or F32;  min / max: F32 for
+ *                 float input, U32 for u32, ignoring NaN; for n = 0 the
+ *                 identities.
  * The sum equals the last inclusive output when there is no carry-in (bit for
  * bit for integers).  Same workspace as tr_scan; dtypes, carry, in-place and
- * timeout rules as tr_scan.  The last tile writes the reduction; its wait for
- * the other tiles' min / max is bounded like the look-back's
- * (TR_ERR_TIMEOUT). */
+ * timeout rules as tr_scan.  The last tile writes the sum; min / max are
+ * folded once per block and written by the last block to finish. */
 tr_status tr_scan_reduce(const tr_map_desc* map, const void* d_x, tr_dtype xt, void* d_y, tr_dtype yt, int64_t n,
                          int mode, const void* d_carry_in, unsigned ops, void* d_sum, tr_dtype sum_t, void* d_min,
                          void* d_max, const tr_exec* exec);

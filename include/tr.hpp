@@ -120,8 +120,8 @@ tr_status segmented_reduce(const F& f, const In* d_x, int64_t n, const int64_t* 
   return segk::launch<In, F>(f, d_x, n, d_off, n_seg, RedOut{d_sums, d_mins, d_maxs, TR_F64, ops}, e);
 }
 
-// Inclusive (or exclusive) scan of f into d_y (FP32, compensated within tiles,
-// FP64 between tiles); d_carry (nullable, device) is added to every output;
+// Inclusive (or exclusive) scan of f into d_y (FP32, float-float within and
+// between tiles); d_carry (nullable, device) is added to every output;
 // the optional sum (FP64) / min / max of f come from the same pass.
 template <class F, class In>
 tr_status scan(const F& f, const In* d_x, float* d_y, int64_t n, const tr_exec* e, int mode = TR_SCAN_INCLUSIVE,
