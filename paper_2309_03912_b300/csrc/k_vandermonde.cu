@@ -533,23 +533,26 @@ __global__ void __launch_bounds__(256) k_vander_join(const ColPart* __restrict__
 // polynomials and its columns points, so a thread owns one polynomial of its
 // warp's lanes and folds that polynomial's values at the warp's 128 points
 // into its running compensated sum, minimum and maximum in registers -- no
-// shared memory and no exchange between lanes.  The unit of work is a pair of
-// polynomial blocks at one point block: the V tile (the powers of the points
+// shared memory and no exchange between lanes.  The unit of work is a group of
+// NB polynomial blocks at one point block: the V tile (the powers of the points
 // and their bf16 split, about half of the non-tensor work) is built once and
-// multiplied by both C tiles in turn.  A CTA walks its units pair-major, so the
-// running results carry over all of its point blocks, and are written to the
-// CTA's workspace slot when the pair changes.  (Measured on B300 at 2^20 points
-// x 4096 polynomials, bf16x3 / bf16x6: one V tile per polynomial block, 1.045 /
-// 1.304 ms.)
+// multiplied by the NB C tiles in turn -- four for bf16x3, two for bf16x6 (its
+// three parts per tile leave shared memory for two).  A CTA walks its units
+// group-major, so the running results carry over all of its point blocks, and
+// are written to the CTA's workspace slot when the group changes.  (Measured on
+// B300 at 2^20 points x 4096 polynomials, bf16x3 / bf16x6: one V tile per
+// polynomial block, 1.045 / 1.304 ms; per two blocks, 0.876 / 1.180 ms.)
 constexpr int kPolyBlk = 128, kPtBlk = 256;
-constexpr int kPairBlk = 2 * kPolyBlk;  // polynomials per unit
+template <int NS>
+constexpr int kGroupBlocks = NS == 2 ? 4 : 2;  // polynomial blocks per unit
 
 template <int NS>
 struct ColLayout {
-  static constexpr uint32_t a = 0;                        // C parts: 2 blocks x NS x 128 polynomials x 32 powers
-  static constexpr uint32_t b = 2 * NS * kABytes;         // V parts: NS x 256 points x 32 powers
-  static constexpr uint32_t comb = b + NS * kBBytes;      // the warps' halves combined: 2 x 4 x 32 ColPart
-  static constexpr uint32_t bar = comb + 2 * 4 * 32 * sizeof(ColPart);
+  static constexpr int NB = kGroupBlocks<NS>;
+  static constexpr uint32_t a = 0;                        // C parts: NB blocks x NS x 128 polynomials x 32 powers
+  static constexpr uint32_t b = NB * NS * kABytes;        // V parts: NS x 256 points x 32 powers
+  static constexpr uint32_t comb = b + NS * kBBytes;      // the warps' halves combined: NB x 4 x 32 ColPart
+  static constexpr uint32_t bar = comb + NB * 4 * 32 * sizeof(ColPart);
   static constexpr uint32_t used = bar + 64;
   static constexpr uint32_t request = used + 1024 > 80 * 1024 ? used + 1024 : 80 * 1024;
   static_assert(request <= 110 * 1024, "two CTAs per SM");
@@ -578,6 +581,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_vander_colred(const float* __
                                                                  const float* __restrict__ coef, int deg,
                                                                  int64_t npoly, ColPart* parts, WsHeader* hdr) {
   using L = ColLayout<NS>;
+  constexpr int NB = L::NB, kGroup = NB * kPolyBlk;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   unsigned char* sA = base + L::a;
@@ -589,8 +593,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_vander_colred(const float* __
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = warp & 3, h = warp >> 2;  // TMEM lanes 32 g .. (polynomials), point half h
   const int64_t m_blocks = (m + kPtBlk - 1) / kPtBlk, p_blocks = (npoly + kPolyBlk - 1) / kPolyBlk;
-  const int64_t pairs = (p_blocks + 1) / 2;
-  const int64_t units = m_blocks * pairs;
+  const int64_t groups = (p_blocks + NB - 1) / NB;
+  const int64_t units = m_blocks * groups;
   const int64_t t_begin = tc_tile_begin(units, blockIdx.x, gridDim.x),
                 t_end = tc_tile_begin(units, blockIdx.x + 1, gridDim.x);
 
@@ -609,27 +613,27 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_vander_colred(const float* __
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  // running results of polynomial 256 pp + 128 s + 32 g + lane (block s of the pair) over the points
-  // of half h seen so far
-  float cs_hi[2], cs_lo[2], cmn[2], cmx[2];
+  // running results of polynomial kGroup pp + 128 s + 32 g + lane (block s of the group) over the
+  // points of half h seen so far
+  float cs_hi[NB], cs_lo[NB], cmn[NB], cmx[NB];
 #pragma unroll
-  for (int s = 0; s < 2; ++s) cs_hi[s] = cs_lo[s] = 0.0f, cmn[s] = INFINITY, cmx[s] = -INFINITY;
+  for (int s = 0; s < NB; ++s) cs_hi[s] = cs_lo[s] = 0.0f, cmn[s] = INFINITY, cmx[s] = -INFINITY;
   auto flush = [&](int64_t pp) {  // both halves combined in FP64 into the slot (CTA + pp)
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < NB; ++s)
       if (h == 1) comb[s * kPolyBlk + g * 32 + lane] = ColPart{(double)cs_hi[s] + (double)cs_lo[s], cmn[s], cmx[s]};
     __syncthreads();
     if (h == 0) {
 #pragma unroll
-      for (int s = 0; s < 2; ++s) {
+      for (int s = 0; s < NB; ++s) {
         const ColPart q = comb[s * kPolyBlk + g * 32 + lane];
-        parts[(blockIdx.x + pp) * kPairBlk + s * kPolyBlk + g * 32 + lane] =
+        parts[(blockIdx.x + pp) * kGroup + s * kPolyBlk + g * 32 + lane] =
             ColPart{((double)cs_hi[s] + (double)cs_lo[s]) + q.sum, fminf(cmn[s], q.mn), fmaxf(cmx[s], q.mx)};
       }
     }
     __syncthreads();
 #pragma unroll
-    for (int s = 0; s < 2; ++s) cs_hi[s] = cs_lo[s] = 0.0f, cmn[s] = INFINITY, cmx[s] = -INFINITY;
+    for (int s = 0; s < NB; ++s) cs_hi[s] = cs_lo[s] = 0.0f, cmn[s] = INFINITY, cmx[s] = -INFINITY;
   };
 
   uint32_t phase = 0;
@@ -646,14 +650,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_vander_colred(const float* __
     const int64_t i0 = qb * kPtBlk;
     if (pp != loaded_p) {
       if (loaded_p >= 0) flush(loaded_p);
-      {  // the two C tiles: polynomial 256 pp + tid (zero beyond npoly), powers 0 .. 31 (zero beyond deg);
-         // threads 0..127 the first block, 128..255 the second
-        const int64_t j = pp * kPairBlk + tid;
+#pragma unroll
+      for (int r = 0; r < NB / 2; ++r) {  // the NB C tiles: polynomial kGroup pp + 256 r + tid (zero beyond
+        // npoly), powers 0 .. 31 (zero beyond deg); threads 0..127 block 2 r, 128..255 block 2 r + 1
+        const int64_t j = pp * kGroup + r * 2 * kPolyBlk + tid;
         const bool in = j < npoly;
         float v[kK];
 #pragma unroll
         for (int k = 0; k < kK; ++k) v[k] = (in && k <= deg) ? __ldg(&coef[(int64_t)k * npoly + j]) : 0.0f;
-        store_split_row<NS>(sA + (tid >> 7) * NS * kABytes, kABytes, tid & (kPolyBlk - 1), v);
+        store_split_row<NS>(sA + (2 * r + (tid >> 7)) * NS * kABytes, kABytes, tid & (kPolyBlk - 1), v);
       }
       loaded_p = pp;
     }
@@ -670,8 +675,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_vander_colred(const float* __
     __syncthreads();
     const int valid = (int)imax<int64_t>(0, imin<int64_t>(128, m - (i0 + h * 128)));
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-      if (2 * pp + s >= p_blocks) break;  // (the last pair of an odd block count has one block)
+    for (int s = 0; s < NB; ++s) {
+      if (NB * pp + s >= p_blocks) break;  // (the last group may hold fewer blocks)
       if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = smem_u32(sA + s * NS * kABytes), b0 = smem_u32(sB);
@@ -744,15 +749,16 @@ tr_status launch_colred(const float* x, int64_t m, const float* coef, int deg, i
   auto kern = k_vander_colred<NS>;
   tr_status s = ensure_dyn_smem((const void*)kern, (int)L::request, "cudaFuncSetAttribute(k_vander_colred)");
   if (s) return s;
-  const int64_t m_blocks = ceil_div(m, kPtBlk), units = m_blocks * ceil_div(ceil_div(npoly, kPolyBlk), 2);
+  constexpr int NB = L::NB;
+  const int64_t m_blocks = ceil_div(m, kPtBlk), units = m_blocks * ceil_div(ceil_div(npoly, kPolyBlk), NB);
   const int64_t grid = std::min<int64_t>(std::min<int64_t>(units, 2 * (int64_t)dev_info().sm_count), kMaxTcGrid);
   ColPart* parts = reinterpret_cast<ColPart*>(ws_body(e));
   cudaStream_t st = stream_of(e);
   kern<<<(unsigned)grid, kTcThreads, L::request, st>>>(x, m, coef, deg, npoly, parts, ws_header(e));
   if ((s = launch_status("k_vander_colred"))) return s;
-  // slot (CTA c, pair pp) at (c + pp) x 256: the join's column blocks are the pairs
-  k_vander_join<<<(unsigned)ceil_div(npoly, 256), 256, 0, st>>>(parts, m_blocks, units, grid, kPairBlk, npoly, colsum,
-                                                               colmin, colmax);
+  // slot (CTA c, group pp) at (c + pp) x NB x 128: the join's column blocks are the groups
+  k_vander_join<<<(unsigned)ceil_div(npoly, 256), 256, 0, st>>>(parts, m_blocks, units, grid, NB * kPolyBlk, npoly,
+                                                               colsum, colmin, colmax);
   return launch_status("k_vander_join");
 }
 
@@ -789,9 +795,10 @@ tr_status launch_tc_ns(int out, bool red, const CUtensorMap& ymap, const float* 
 }
 
 // Slots of either form: (grid + column blocks) x block width, at most
-// (kMaxTcGrid + npoly / 128 + 1) x 256 entries.
+// (kMaxTcGrid + npoly / 128 + 1) x 512 entries (column blocks of up to 512
+// polynomials).
 size_t vander_ws_bytes(int64_t npoly) {
-  return (size_t)kWsHeader + (size_t)(kMaxTcGrid + ceil_div(std::max<int64_t>(npoly, 1), kPolyBlk)) * kTileN *
+  return (size_t)kWsHeader + (size_t)(kMaxTcGrid + ceil_div(std::max<int64_t>(npoly, 1), kPolyBlk)) * 4 * kPolyBlk *
                                  sizeof(ColPart);
 }
 
