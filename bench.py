@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--no-configs", action="store_true", help="headline only")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     p.add_argument("--only", default="", help="comma-separated names of the extra configurations to run "
-                                              "(scan_u32, scan_f32, rational_reduce, reduce_f64, mixers_2^20, batched, vandermonde, f16); "
+                                              "(scan_u32, scan_f32, rational_reduce, map, reduce_f64, mixers_2^20, batched, vandermonde, f16); "
                                               "skips the headline")
     p.add_argument("--config-log2", type=int, default=28, help="log2 size of the 2^28 scan configurations")
     p.add_argument("--f16-log2", type=int, default=30, help="log2 size of the FP16-storage configuration")
@@ -399,6 +399,18 @@ def other_configs(args, stream, hbm_peak, tensor_peak=1781.3):
                         "got": (float(sr.item()), float(mmr[0].item()), float(mmr[1].item()))}
         del xrd
 
+    if want('map'):
+        # y = f(x) alone: the headline's map over its 2^28 inputs (read 1 GiB, write 1 GiB)
+        xm_, mm_, _ = I.rational_segments(N_HEAD, NSEG_HEAD)
+        xmd = torch.from_numpy(xm_).cuda()
+        ym = torch.empty_like(xmd)
+        exm = B.make_exec(None, stream=stream)
+        ms, _, _ = time_launches(lambda: B.tr_map(mm_, xmd, ym, exm), steps, warm, stream)
+        name = "map_rational66_2^28"
+        record(name, ms, xmd.numel(), xmd.numel() * 8, 1)
+        checks[name] = {"kind": "map_rational", "x": xm_, "map": mm_, "got": ym.cpu().numpy()}
+        del xmd, ym
+
     if want('scan_f32'):
         # f32 compensated scan of x^2, N = 2^28
         xf = I.square_f32(big)
@@ -629,6 +641,12 @@ def check_configs(checks, threads):
             red_ok = [int(v) for v in c["red"]] == [rs % (1 << 32), rlo, rhi]
             errs[name] = {"mismatches": bad + (0 if red_ok else 1), "bar": 0, "pass": bad == 0 and red_ok,
                           "checked": f"all {c['x'].size} outputs and the sum, min, max, bit for bit"}
+        elif k == "map_rational":
+            m = c["map"]
+            ref = oracle.map_values_f32(oracle.MapSpec(m["kind"], m["cp"], m["cq"]), c["x"])
+            bad = int(np.count_nonzero(c["got"].astype(np.float64) != ref))
+            errs[name] = {"mismatches": bad, "bar": 0, "pass": bad == 0,
+                          "checked": f"all {c['x'].size} outputs against the map in binary32, bit for bit"}
         elif k == "reduce_rational":
             m = c["map"]
             spec = oracle.MapSpec(m["kind"], m["cp"], m["cq"])
