@@ -84,6 +84,25 @@ def test_map_float(orc, B, mi, dt, n, off):
     assert np.array_equal(got.view(np.int64), orc.map_values_f32(oracle_map(orc, m), xh).view(np.int64))
 
 
+@pytest.mark.parametrize("deg", [0, 1, 3, 5, 13, 16, 17, 24])
+def test_horner_runtime_degrees(orc, B, deg):
+    """Horner maps of run-time degree (packed up to degree 16, the coefficient
+    loop above): map bit for bit against the binary32 oracle map; reduce within
+    1e-6 of the exact sum of those values, min / max exact."""
+    g = np.random.default_rng(300 + deg)
+    m = I.horner_map(I.f32_exact(g.standard_normal(deg + 1) / (np.arange(deg + 1) + 1.0)))
+    n = 100_003
+    xh = g.uniform(-1.2, 1.2, n).astype(np.float32)
+    x = torch.from_numpy(xh).cuda()
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    B.tr_map(m, x, y)
+    f32 = orc.map_values_f32(oracle_map(orc, m), xh)
+    assert np.array_equal(y.cpu().double().numpy().view(np.int64), f32.view(np.int64))
+    s, lo, hi = reduce_dev(B, m, x)
+    rs, rlo, rhi, ra = orc.reduce_float_mt(oracle_map(orc, m), xh, f32=True)
+    assert abs(s - rs) <= 1e-6 * ra and lo == rlo and hi == rhi
+
+
 @pytest.mark.parametrize("mi", range(len(MAPS)), ids=MAP_IDS)
 def test_map_f64_bitexact(orc, B, mi):
     """FP64 device evaluation = FP64 oracle, bit for bit (same fma/division sequence)."""
@@ -277,7 +296,7 @@ def test_scan_square_f32(orc, B, dt, n, off):
     assert np.all(np.abs(got - ref) <= 1e-5 * np.abs(ref) + 1e-38)
 
 
-@pytest.mark.parametrize("mi", [2, 4, 6], ids=["horner8", "rational66", "newton6"])
+@pytest.mark.parametrize("mi", [2, 3, 4, 6], ids=["horner8", "horner11", "rational66", "newton6"])
 def test_scan_general_sign(orc, B, mi):
     """Mixed-sign f: |y_i - ref_i| <= 2^-23 |ref_i| + 1e-6 sum_{j<=i} |f_j| + sum_{j<=i} bound_j."""
     m = MAPS[mi]
