@@ -166,22 +166,29 @@ __global__ void __launch_bounds__(kThreads) k_segreduce(const In* __restrict__ x
 template <class F>
 struct SegShape {  // division-bound maps (rational, Newton) and the rest
   static constexpr int ring = 8192, blocks = 3, sub = 2;
+  // warp ranges per resident warp: twice as many, half as long, run in two waves (measured on B300 for
+  // rational 6/6 at 2^28: 267 us against 272 us with one range per resident warp; four: 267 us)
+  static constexpr int waves = 2;
 };
 template <class T>
 struct SegShape<Identity<T>> {
   static constexpr int ring = 16384, blocks = 1, sub = 1;
+  static constexpr int waves = 1;
 };
 template <class T>
 struct SegShape<Square<T>> {
   static constexpr int ring = 16384, blocks = 1, sub = 1;
+  static constexpr int waves = 1;
 };
 template <class T, int D>
 struct SegShape<Horner<T, D>> {
   static constexpr int ring = 8192, blocks = 2, sub = 1;
+  static constexpr int waves = 1;
 };
 template <class T>
 struct SegShape<HornerN<T>> {
   static constexpr int ring = 8192, blocks = 2, sub = 1;
+  static constexpr int waves = 1;
 };
 constexpr int kMaxStages = 16;
 constexpr uint64_t kTmaWaitNs = 1000000000ull;         // 1 s for one bulk copy before giving up
@@ -418,7 +425,7 @@ tr_status launch(const Src& P, const In* x, int64_t n, const int64_t* off, int64
     if (s) return s;
   }
   const int64_t resident = (int64_t)dev_info().sm_count * blocks_per_sm((const void*)kern, kThreads, smem);
-  const int64_t grid_full = std::min<int64_t>(resident, kMaxGrid);
+  const int64_t grid_full = std::min<int64_t>(resident * (tma ? SegShape<F>::waves : 1), kMaxGrid);
   const int64_t quantum = 32 * V;  // range starts stay 16-byte aligned
   int64_t range = ceil_div(std::max<int64_t>(n, 1), grid_full * kWarps);
   range = ceil_div(range, quantum) * quantum;
