@@ -454,7 +454,8 @@ def other_configs(args, stream, hbm_peak, tensor_peak=1781.3):
         # the mix's roofline: the larger of the HBM time of its bytes and the FMA-pipe time of its
         # arithmetic, counted per element from each map's operation sequence (FP32 lane operations on
         # the FMA pipe: Horner degree d: d fmas + 1 for the compensated sum; rational dp/dq: dp + dq
-        # fmas + 6 for the correctly rounded quotient + 1; Newton, I steps: 11 I + 1), and of its
+        # fmas + 6 for the correctly rounded quotient + 1; Newton, I steps: 10 per step (the square, five for
+        # the negated quotient, the step, three for the division by 3), one sign at the end, 1), and of its
         # reciprocals on the XU pipe (one per quotient)
         props = torch.cuda.get_device_properties(0)
         clock_hz = 2.032e9
@@ -465,7 +466,7 @@ def other_configs(args, stream, hbm_peak, tensor_peak=1781.3):
             elif m["kind"] == "rational":
                 f_, x_, label = (len(m["cp"]) - 1) + (len(m["cq"]) - 1) + 7, 1, "rational"
             else:
-                f_, x_, label = 11 * m["iters"] + 1, m["iters"], "newton_cbrt"
+                f_, x_, label = 10 * m["iters"] + 2, m["iters"], "newton_cbrt"
             fma_ops += f_ * int(L)
             xu_ops += x_ * int(L)
             d = per_map.setdefault(label, {"elements": 0, "fma_lane_ops": 0})

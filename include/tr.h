@@ -267,7 +267,8 @@ typedef struct tr_batch_plan tr_batch_plan; /* opaque, owned by the library */
  * finishes an array's last item joins its partials in FP64 in item order, so
  * results are bitwise deterministic.  autotune != 0 times the launch shapes
  * -- item size T in {8K, 16K, 32K, 64K}, 128 or 256 threads, items equal in
- * elements or balanced by map cost -- on this data (it writes the outputs and
+ * elements or balanced by map cost, 4 or 2 16-byte vectors in flight per lane
+ * (fewer registers, more resident warps) -- on this data (it writes the outputs and
  * synchronises the device; TR_AUTOTUNE_CACHE names an optional cache file);
  * 0 takes a fixed default.  Plan creation allocates the plan's device buffers
  * and instantiates the graph; the arrays and outputs must stay valid while

@@ -17,8 +17,10 @@
 // therefore independent of scheduling: bitwise deterministic.
 //
 // Graph: a memset of the queue head and the kernel, captured once; each run is
-// one cudaGraphLaunch.  Tile size T and block size come from a small
-// autotuner that times the candidates on the plan's own data.
+// one cudaGraphLaunch.  Tile size T, block size, cost balancing and the
+// vectors per lane (4 or 2: registers, hence resident warps, against loads in
+// flight) come from a small autotuner that times the candidates on the plan's
+// own data.  The device side is in batched_kernel.cuh.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -30,184 +32,16 @@
 #include <string>
 #include <vector>
 
-#include "accum.cuh"
-#include "dispatch.cuh"
-#include "range.cuh"
+#include "batched_kernel.cuh"
 
 namespace tr {
 
+BatchedKernel batched_kernel_u4(tr_dtype xt, int threads) { return batched_kernel<4>(xt, threads); }
+
 namespace {
 
-struct BatchArray {
-  const void* x;  // storage type of the plan
-  int64_t len;
-  int32_t kind, deg_p, deg_q, iters;
-  int32_t first_slot, n_items;
-  int32_t aligned, pad;
-  float cp[TR_MAX_DEGREE + 1];
-  float cq[TR_MAX_DEGREE + 1];
-};
-
-struct BatchItem {
-  int32_t array;
-  int32_t slot;  // partial slot of this item (array's first slot + its index)
-  int64_t start;
-  int64_t count;
-};
-
-struct BatchPartial {
-  double sum;
-  float mn, mx;
-};
-
-struct BatchOut {
-  double* sums;
-  float* mins;
-  float* maxs;
-  unsigned ops;
-};
-
-template <class F>
-struct MakeBatchMap {
-  __device__ __forceinline__ static F make(const BatchArray&) { return F{}; }
-};
-template <int D>
-struct MakeBatchMap<Horner<float, D>> {
-  __device__ __forceinline__ static Horner<float, D> make(const BatchArray& A) {
-    Horner<float, D> h{};
-#pragma unroll
-    for (int k = 0; k <= D; ++k) h.c[k] = A.cp[k];
-    return h;
-  }
-};
-template <>
-struct MakeBatchMap<HornerN<float>> {
-  __device__ __forceinline__ static HornerN<float> make(const BatchArray& A) { return HornerN<float>{A.cp, A.deg_p}; }
-};
-template <>
-struct MakeBatchMap<Rational<float, 6, 6>> {
-  __device__ __forceinline__ static Rational<float, 6, 6> make(const BatchArray& A) {
-    Rational<float, 6, 6> r{};
-#pragma unroll
-    for (int k = 0; k <= 6; ++k) {
-      r.p[k] = A.cp[k];
-      r.q[k] = A.cq[k];
-    }
-    return r;
-  }
-};
-template <>
-struct MakeBatchMap<RationalN<float>> {
-  __device__ __forceinline__ static RationalN<float> make(const BatchArray& A) {
-    return RationalN<float>{A.cp, A.cq, A.deg_p, A.deg_q};
-  }
-};
-template <>
-struct MakeBatchMap<NewtonCbrt<float, -1>> {
-  __device__ __forceinline__ static NewtonCbrt<float, -1> make(const BatchArray& A) {
-    NewtonCbrt<float, -1> m{};
-    m.iters = A.iters;
-    return m;
-  }
-};
-
-template <class In, class F>
-__device__ __forceinline__ Acc<float> run_item(const BatchArray& A, const BatchItem& it, int lane) {
-  const auto f = Packed<F>::make(MakeBatchMap<F>::make(A));  // coefficient pairs in registers
-  return warp_reduce_range<In>(static_cast<const In*>(A.x), it.start, it.start + it.count, A.aligned, f, lane,
-                               it.start + it.count);
-}
-
-template <class In>
-__device__ __noinline__ Acc<float> dispatch_item(const BatchArray& A, const BatchItem& it, int lane) {
-  switch (A.kind) {
-    case TR_MAP_HORNER:
-      switch (A.deg_p) {
-        case 4: return run_item<In, Horner<float, 4>>(A, it, lane);
-        case 5: return run_item<In, Horner<float, 5>>(A, it, lane);
-        case 6: return run_item<In, Horner<float, 6>>(A, it, lane);
-        case 7: return run_item<In, Horner<float, 7>>(A, it, lane);
-        case 8: return run_item<In, Horner<float, 8>>(A, it, lane);
-        case 9: return run_item<In, Horner<float, 9>>(A, it, lane);
-        case 10: return run_item<In, Horner<float, 10>>(A, it, lane);
-        case 11: return run_item<In, Horner<float, 11>>(A, it, lane);
-        case 12: return run_item<In, Horner<float, 12>>(A, it, lane);
-        case 13: return run_item<In, Horner<float, 13>>(A, it, lane);
-        case 14: return run_item<In, Horner<float, 14>>(A, it, lane);
-        case 15: return run_item<In, Horner<float, 15>>(A, it, lane);
-        case 16: return run_item<In, Horner<float, 16>>(A, it, lane);
-        default: return run_item<In, HornerN<float>>(A, it, lane);
-      }
-    case TR_MAP_RATIONAL:
-      if (A.deg_p == 6 && A.deg_q == 6) return run_item<In, Rational<float, 6, 6>>(A, it, lane);
-      return run_item<In, RationalN<float>>(A, it, lane);
-    case TR_MAP_NEWTON_CBRT:
-      if (A.iters == 6) return run_item<In, NewtonCbrt<float, 6>>(A, it, lane);
-      return run_item<In, NewtonCbrt<float, -1>>(A, it, lane);
-    case TR_MAP_SQUARE: return run_item<In, Square<float>>(A, it, lane);
-    default: return run_item<In, Identity<float>>(A, it, lane);
-  }
-}
-
-__device__ __forceinline__ void store_batch(const BatchOut& o, int64_t a, double s, float mn, float mx) {
-  if ((o.ops & TR_SUM) && o.sums) o.sums[a] = s;
-  if ((o.ops & TR_MIN) && o.mins) o.mins[a] = mn;
-  if ((o.ops & TR_MAX) && o.maxs) o.maxs[a] = mx;
-}
-
-template <class In, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_batched(const BatchArray* __restrict__ arrays,
-                                                     const BatchItem* __restrict__ items, int32_t n_items,
-                                                     BatchPartial* partials, uint32_t* counters, uint32_t* queue,
-                                                     BatchOut out) {
-  const int lane = threadIdx.x & 31;
-  while (true) {
-    int32_t i = 0;
-    if (lane == 0) i = (int32_t)atomicAdd(queue, 1u);
-    i = __shfl_sync(kFull, i, 0);
-    if (i >= n_items) break;
-    const BatchItem it = items[i];
-    const BatchArray& A = arrays[it.array];
-    const Acc<float>::W w = dispatch_item<In>(A, it, lane).warp();
-    const int32_t n_it = A.n_items;
-    if (n_it == 1) {
-      if (lane == 0) store_batch(out, it.array, ff_to_double(w.s), w.mn, w.mx);
-      continue;
-    }
-    int last = 0;
-    if (lane == 0) {
-      partials[it.slot] = BatchPartial{ff_to_double(w.s), w.mn, w.mx};
-      __threadfence();
-      last = atomicAdd(&counters[it.array], 1u) == (uint32_t)(n_it - 1);
-    }
-    last = __shfl_sync(kFull, last, 0);
-    if (!last) continue;
-    __threadfence();
-    double s = 0.0;
-    float mn = INFINITY, mx = -INFINITY;
-    for (int j = lane; j < n_it; j += 32) {  // fixed order: lane j takes slots j, j+32, ...
-      const BatchPartial* p = &partials[A.first_slot + j];
-      s += __ldcg(&p->sum);
-      mn = fminf(mn, __ldcg(&p->mn));
-      mx = fmaxf(mx, __ldcg(&p->mx));
-    }
-    s = warp_sum(s);
-    mn = warp_min(mn);
-    mx = warp_max(mx);
-    if (lane == 0) {
-      store_batch(out, it.array, s, mn, mx);
-      counters[it.array] = 0;  // ready for the next run
-    }
-  }
-}
-
-typedef void (*BatchedKernel)(const BatchArray*, const BatchItem*, int32_t, BatchPartial*, uint32_t*, uint32_t*,
-                              BatchOut);
-
-BatchedKernel kernel_for(tr_dtype xt, int threads) {
-  if (xt == TR_F16) return threads == 128 ? k_batched<__half, 128> : k_batched<__half, 256>;
-  if (xt == TR_BF16) return threads == 128 ? k_batched<__nv_bfloat16, 128> : k_batched<__nv_bfloat16, 256>;
-  return threads == 128 ? k_batched<float, 128> : k_batched<float, 256>;
+BatchedKernel kernel_for(tr_dtype xt, int threads, int unroll) {
+  return unroll == 2 ? batched_kernel_u2(xt, threads) : batched_kernel_u4(xt, threads);
 }
 
 // rough per-element instruction cost of a map, for ordering the queue
@@ -220,13 +54,16 @@ double map_cost(const tr_map_desc& m) {
   }
 }
 
-// Autotuned launch shape: the work-item size T, the block size, and whether
+// Autotuned launch shape: the work-item size T, the block size, whether
 // items are balanced by map cost (an array's items then hold about
-// T x cost(Horner 8) / cost(map) elements, so costly maps get shorter items).
+// T x cost(Horner 8) / cost(map) elements, so costly maps get shorter items),
+// and the 16-byte vectors each lane has in flight (4 or 2).  The grid is the
+// kernel's full occupancy, which the vectors per lane set through registers.
 struct Config {
   int64_t tile = 32768;
   int threads = 256;
   int balance = 0;
+  int unroll = 4;
 };
 
 }  // namespace
@@ -320,14 +157,14 @@ tr_status enqueue(tr_batch_plan* p, cudaStream_t st) {
   tr_status s = cuda_status(cudaMemsetAsync(p->d_counters + p->n_arrays, 0, sizeof(uint32_t), st), "memset(queue)");
   if (s) return s;
   const BatchOut out{p->sums, p->mins, p->maxs, p->ops};
-  kernel_for(p->xt, p->cfg.threads)<<<p->grid, p->cfg.threads, 0, st>>>(p->d_arrays, p->d_items, p->n_items, p->d_partials,
+  kernel_for(p->xt, p->cfg.threads, p->cfg.unroll)<<<p->grid, p->cfg.threads, 0, st>>>(p->d_arrays, p->d_items, p->n_items, p->d_partials,
                                                                   p->d_counters, p->d_counters + p->n_arrays, out);
   return launch_status("k_batched");
 }
 
 tr_status set_config(tr_batch_plan* p, const Config& c) {
   p->cfg = c;
-  const BatchedKernel k = kernel_for(p->xt, c.threads);
+  const BatchedKernel k = kernel_for(p->xt, c.threads, c.unroll);
   p->grid = dev_info().sm_count * blocks_per_sm((const void*)k, c.threads);
   return build_items(p, c.tile, c.balance);
 }
@@ -366,13 +203,16 @@ bool cache_lookup(const std::string& key, Config* c) {
   std::ifstream f(path);
   std::string line;
   while (std::getline(f, line)) {
+    // key, tile, threads, balance[, vectors per lane]
     const size_t t1 = line.find('\t'), t2 = line.find('\t', t1 + 1), t3 = line.find('\t', t2 + 1);
     if (t1 == std::string::npos || t2 == std::string::npos || t3 == std::string::npos) continue;
     if (line.substr(0, t1) == key) {
+      const size_t t4 = line.find('\t', t3 + 1);
       c->tile = atoll(line.substr(t1 + 1, t2 - t1 - 1).c_str());
       c->threads = atoi(line.substr(t2 + 1, t3 - t2 - 1).c_str());
-      c->balance = atoi(line.substr(t3 + 1).c_str()) != 0;
-      return c->tile > 0 && (c->threads == 128 || c->threads == 256);
+      c->balance = atoi(line.substr(t3 + 1, t4 == std::string::npos ? std::string::npos : t4 - t3 - 1).c_str()) != 0;
+      c->unroll = t4 == std::string::npos ? 4 : atoi(line.substr(t4 + 1).c_str());
+      return c->tile > 0 && (c->threads == 128 || c->threads == 256) && (c->unroll == 2 || c->unroll == 4);
     }
   }
   return false;
@@ -382,7 +222,7 @@ void cache_store(const std::string& key, const Config& c) {
   const char* path = getenv("TR_AUTOTUNE_CACHE");
   if (!path) return;
   std::ofstream f(path, std::ios::app);
-  f << key << '\t' << c.tile << '\t' << c.threads << '\t' << c.balance << '\n';
+  f << key << '\t' << c.tile << '\t' << c.threads << '\t' << c.balance << '\t' << c.unroll << '\n';
 }
 
 tr_status capture(tr_batch_plan* p, bool unbatched, cudaGraphExec_t* out);
@@ -482,22 +322,24 @@ tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, cons
     int tried = 0;
     for (int64_t T : {8192, 16384, 32768, 65536})
       for (int th : {128, 256})
-        for (int bal : {0, 1}) {
-          Config c;
-          c.tile = T;
-          c.threads = th;
-          c.balance = bal;
-          float ms = 0.f;
-          if ((s = set_config(p, c)) || (s = time_config(p, st, &ms))) {
-            tr_batched_plan_destroy(p);
-            return s;
+        for (int bal : {0, 1})
+          for (int u : {4, 2}) {
+            Config c;
+            c.tile = T;
+            c.threads = th;
+            c.balance = bal;
+            c.unroll = u;
+            float ms = 0.f;
+            if ((s = set_config(p, c)) || (s = time_config(p, st, &ms))) {
+              tr_batched_plan_destroy(p);
+              return s;
+            }
+            ++tried;
+            if (ms < best_ms) {
+              best_ms = ms;
+              best = c;
+            }
           }
-          ++tried;
-          if (ms < best_ms) {
-            best_ms = ms;
-            best = c;
-          }
-        }
     cache_store(key, best);
     char b[96];
     snprintf(b, sizeof b, "autotuned over %d candidates (best %.3f ms)", tried, best_ms);
@@ -512,8 +354,9 @@ tr_status tr_batched_plan_create(int64_t n_arrays, const void* const* d_xs, cons
     return s;
   }
   char b[256];
-  snprintf(b, sizeof b, "tile=%lld threads=%d balance=%d grid=%d items=%d arrays=%lld (%s)", (long long)best.tile,
-           best.threads, best.balance, p->grid, p->n_items, (long long)n_arrays, how.c_str());
+  snprintf(b, sizeof b, "tile=%lld threads=%d balance=%d vectors_per_lane=%d grid=%d items=%d arrays=%lld (%s)",
+           (long long)best.tile, best.threads, best.balance, best.unroll, p->grid, p->n_items, (long long)n_arrays,
+           how.c_str());
   p->desc = b;
   *out = p;
   return TR_OK;

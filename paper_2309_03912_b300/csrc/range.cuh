@@ -1,7 +1,8 @@
 // range.cuh -- one warp reduces f over the elements [pa, pb) of an array:
-// 128-bit loads with kRangeUnroll vectors in flight per lane, a scalar head
-// and tail around the 16-byte-aligned body, the map in registers, and the
-// per-lane Kahan-compensated accumulator of accum.cuh.  Every lane returns
+// 128-bit loads with U vectors in flight per lane (kRangeUnroll unless the
+// caller picks another count; fewer vectors take fewer registers), a scalar
+// head and tail around the 16-byte-aligned body, the map in registers, and
+// the per-lane Kahan-compensated accumulator of accum.cuh.  Every lane returns
 // its own accumulator; combine with Acc<float>::warp().  While it streams,
 // lane 0 asks L2 for the data kPrefetchAhead chunks ahead (up to element
 // pf_limit, the end of the region this warp will read).
@@ -12,10 +13,10 @@
 namespace tr {
 
 constexpr int kRangeUnroll = 4;
-// Chunks (32 lanes x kRangeUnroll vectors) requested into L2 ahead of use.
+// Chunks (32 lanes x U vectors) requested into L2 ahead of use.
 constexpr int kPrefetchAhead = 4;
 
-template <class In, class F>
+template <class In, class F, int U = kRangeUnroll>
 __device__ __forceinline__ Acc<float> warp_reduce_range(const In* __restrict__ x, int64_t pa, int64_t pb, int x_aligned,
                                                         const F& f, int lane, int64_t pf_limit) {
   using S = Storage<In>;
@@ -32,19 +33,19 @@ __device__ __forceinline__ Acc<float> warp_reduce_range(const In* __restrict__ x
   const uint4* xv = reinterpret_cast<const uint4*>(x);
   int64_t v = va + lane;
   const int64_t vpf_end = pf_limit / V;  // prefetches stay below element pf_limit
-  for (; v + 32 * (kRangeUnroll - 1) < vb; v += 32 * kRangeUnroll) {
+  for (; v + 32 * (U - 1) < vb; v += 32 * U) {
     if (lane == 0) {
-      const int64_t pv = v + (int64_t)kPrefetchAhead * 32 * kRangeUnroll;
-      if (pv + 32 * kRangeUnroll <= vpf_end) prefetch_l2(xv + pv, 32 * kRangeUnroll * 16);
+      const int64_t pv = v + (int64_t)kPrefetchAhead * 32 * U;
+      if (pv + 32 * U <= vpf_end) prefetch_l2(xv + pv, 32 * U * 16);
     }
-    uint4 raw[kRangeUnroll];
+    uint4 raw[U];
 #pragma unroll
-    for (int u = 0; u < kRangeUnroll; ++u) raw[u] = ld_stream(xv + v + 32 * u);
-    float e[kRangeUnroll * V];
+    for (int u = 0; u < U; ++u) raw[u] = ld_stream(xv + v + 32 * u);
+    float e[U * V];
 #pragma unroll
-    for (int u = 0; u < kRangeUnroll; ++u) S::unpack(raw[u], e + u * V);
-    map_vec<kRangeUnroll * V>(f, e);
-    acc.template add_vec<kRangeUnroll * V>(e);
+    for (int u = 0; u < U; ++u) S::unpack(raw[u], e + u * V);
+    map_vec<U * V>(f, e);
+    acc.template add_vec<U * V>(e);
   }
   for (; v < vb; v += 32) {
     float e[V];

@@ -4,12 +4,15 @@
 // library; it is test infrastructure and no product code links it.
 //
 //   div_check_rcp_invariance : rcp.approx is sign- and scale-invariant over
-//                              every normal input of the fast domain's range;
+//                              every normal input of the fast domain's range
+//                              (rcp(-b) = -rcp(b), rcp(b 2^k) = rcp(b) 2^-k);
 //   div_check_significands   : div_vec<2> (the packed path the kernels run)
-//                              equals a / b for every pair of significands in
+//                              equals a / b, and div_vec_neg<2> equals
+//                              -(a / b), for every pair of significands in
 //                              [1, 2) x [b_first, b_first + b_count) x 2^-23;
-//   div_check_values         : div_hd and div_vec<2> equal a / b (bitwise, NaN
-//                              matched as NaN) on caller-supplied operands.
+//   div_check_values         : div_hd and div_vec<2> equal a / b, and
+//                              div_vec_neg<2> equals -(a / b) (bitwise, NaN
+//                              matched as NaN), on caller-supplied operands.
 #include <cstdint>
 
 #include "common.cuh"
@@ -46,7 +49,10 @@ __global__ void k_rcp(unsigned long long base, Report* rep) {
   const float b = __uint_as_float(u);
   const float m = __uint_as_float((u & 0x807fffffu) | 0x3f800000u);  // sign * significand
   const float scale = __uint_as_float((unsigned)(254 - ex) << 23);  // 2^-(ex - 127), exact
-  if (__float_as_uint(tr::rcp_approx(b)) != __float_as_uint(__fmul_rn(tr::rcp_approx(m), scale))) record(rep, b, m);
+  const float y = tr::rcp_approx(b);
+  if (__float_as_uint(y) != __float_as_uint(__fmul_rn(tr::rcp_approx(m), scale)) ||
+      __float_as_uint(tr::rcp_approx(-b)) != (__float_as_uint(y) ^ 0x80000000u))
+    record(rep, b, m);
 }
 
 // one block per divisor significand, threads over the dividend significands
@@ -55,10 +61,13 @@ __global__ void __launch_bounds__(256) k_sig(unsigned b_first, Report* rep) {
   for (unsigned j = 2 * threadIdx.x; j < (1u << 23); j += 512) {
     const float a[2] = {__uint_as_float(0x3f800000u | j), __uint_as_float(0x3f800000u | (j + 1))};
     const float bb[2] = {b, b};
-    float q[2];
+    float q[2], nq[2];
     tr::div_vec<2>(a, bb, q);
-    if (__float_as_uint(q[0]) != __float_as_uint(__fdiv_rn(a[0], b))) record(rep, a[0], b);
-    if (__float_as_uint(q[1]) != __float_as_uint(__fdiv_rn(a[1], b))) record(rep, a[1], b);
+    tr::div_vec_neg<2>(a, bb, nq, a[0], a[1]);  // a[0] < a[1], both in [1, 2)
+    for (int t = 0; t < 2; ++t) {
+      const unsigned ref = __float_as_uint(__fdiv_rn(a[t], b));
+      if (__float_as_uint(q[t]) != ref || __float_as_uint(nq[t]) != (ref ^ 0x80000000u)) record(rep, a[t], b);
+    }
   }
 }
 
@@ -67,11 +76,15 @@ __global__ void k_values(const float* a, const float* b, int64_t n, Report* rep)
   if (2 * i + 1 >= n + 1) return;
   const int64_t j = 2 * i + 1 < n ? 2 * i + 1 : 2 * i;  // odd n: the last pair repeats its element
   const float aa[2] = {a[2 * i], a[j]}, bb[2] = {b[2 * i], b[j]};
-  float q[2];
+  float q[2], nq[2];
   tr::div_vec<2>(aa, bb, q);
+  const float alo = fminf(fabsf(aa[0]), fabsf(aa[1])), ahi = fmaxf(fabsf(aa[0]), fabsf(aa[1]));
+  // a NaN operand must fail the guard, as it does in the callers (their scans propagate NaN)
+  const bool nan = aa[0] != aa[0] || aa[1] != aa[1];
+  tr::div_vec_neg<2>(aa, bb, nq, nan ? __int_as_float(0x7fffffff) : alo, nan ? __int_as_float(0x7fffffff) : ahi);
   for (int t = 0; t < 2; ++t) {
     const float ref = __fdiv_rn(aa[t], bb[t]);
-    if (!same(q[t], ref) || !same(tr::div_hd(aa[t], bb[t]), ref)) record(rep, aa[t], bb[t]);
+    if (!same(q[t], ref) || !same(tr::div_hd(aa[t], bb[t]), ref) || !same(nq[t], -ref)) record(rep, aa[t], bb[t]);
   }
 }
 

@@ -152,3 +152,54 @@ def test_batched_low_precision_storage(orc, B, dt):
         assert abs(s2[a] - rs) <= 1e-6 * ra + 1e-30, a
     plan.close()
     plan2.close()
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float16], ids=["f32", "f16"])
+@pytest.mark.parametrize("threads,vectors", [(128, 2), (256, 2), (128, 4), (256, 4)])
+def test_every_launch_shape_matches_oracle(orc, B, dt, threads, vectors, tmp_path, monkeypatch):
+    """Each block size and count of vectors in flight per lane (the kernel's
+    two instantiations), forced through the autotune cache: every array
+    against the oracle's binary32 map of its stored values (sums within 1e-6
+    normwise, min / max exact)."""
+    xs, maps = _workload(150, 15)
+    dev = [torch.from_numpy(x).to(dt).cuda() for x in xs]
+    n = len(xs)
+    out = [torch.zeros(n, dtype=torch.float64, device="cuda")] + \
+          [torch.zeros(n, dtype=torch.float32, device="cuda") for _ in range(2)]
+    cache = tmp_path / "tune.tsv"
+    monkeypatch.setenv("TR_AUTOTUNE_CACHE", str(cache))
+    B.BatchPlan(dev, maps, *out, autotune=True).close()  # writes this workload's cache line
+    key = cache.read_text().splitlines()[0].split("\t")[0]
+    cache.write_text(f"{key}\t8192\t{threads}\t1\t{vectors}\n")
+    plan = B.BatchPlan(dev, maps, *out, autotune=True)
+    d = plan.describe()
+    assert "cache" in d and f"threads={threads}" in d and f"vectors_per_lane={vectors}" in d, d
+    for t in out:
+        t.zero_()
+    plan.run()
+    torch.cuda.synchronize()
+    s, lo, hi = (t.cpu().numpy() for t in out)
+    for a, (x, m) in enumerate(zip(dev, maps)):
+        xv = x.cpu().double().numpy()
+        rs, rlo, rhi, ra = orc.reduce_float_mt(oracle_map(orc, m), xv, 1, f32=True)
+        assert abs(s[a] - rs) <= 1e-6 * ra + 1e-30, (a, m["kind"])
+        if xv.size:
+            assert lo[a] == rlo and hi[a] == rhi, a
+        else:
+            assert s[a] == 0 and np.isposinf(lo[a]) and np.isneginf(hi[a])
+    plan.close()
+
+
+def test_cache_line_without_vectors_field_reads_as_four(B, batch, tmp_path, monkeypatch):
+    """A cache line of the older four-field form (no vectors per lane) is still
+    served, with four vectors per lane."""
+    xs, maps, dev, sums, mins, maxs = batch
+    cache = tmp_path / "tune.tsv"
+    monkeypatch.setenv("TR_AUTOTUNE_CACHE", str(cache))
+    B.BatchPlan(dev, maps, sums, mins, maxs, autotune=True).close()
+    key = cache.read_text().splitlines()[0].split("\t")[0]
+    cache.write_text(f"{key}\t16384\t128\t0\n")
+    plan = B.BatchPlan(dev, maps, sums, mins, maxs, autotune=True)
+    d = plan.describe()
+    assert "cache" in d and "tile=16384" in d and "vectors_per_lane=4" in d, d
+    plan.close()

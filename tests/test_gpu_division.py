@@ -9,8 +9,10 @@ point in Sec. 2.3 and 2.6) rests on three checks made here on the GPU:
 
   * the hardware reciprocal is sign- and scale-invariant over every normal
     input whose reciprocal is normal (all 2^32 bit patterns);
-  * the packed quotient equals a / b for every pair of significands in
-    [1, 2) x [1, 2) (all 2^46 pairs, about a minute on a B300);
+  * the packed quotient equals a / b, and the negated form the Newton map
+    runs on its negated iterate equals -(a / b), for every pair of
+    significands in [1, 2) x [1, 2) (all 2^46 pairs, about a minute on a
+    B300);
   * on the fast domain every intermediate stays normal (or is an exactly
     representable remainder), so the sequence commutes with scaling a and b by
     powers of two and with their signs: the two exhaustive checks then cover
