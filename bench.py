@@ -244,22 +244,24 @@ def headline(args, rank, world, stream):
             raise B.TrError(st, L.tr_last_error().decode())
 
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-        B.tr_check(ex)
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
         clk = Clocks(torch.cuda.current_device())
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-        launches0 = B.tr_launch_count()
         with clk:
+            # the warm-up steps run right before the timed ones (the sampler's start-up pause comes first,
+            # so the GPU does not sit idle between warm-up and timing)
+            for _ in range(args.warmup):
+                step()
+            B.tr_check(ex)
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            launches0 = B.tr_launch_count()
             evs[0].record(stream)
             for i in range(args.steps):
                 step()
                 evs[i + 1].record(stream)
             torch.cuda.synchronize()
-        launches = B.tr_launch_count() - launches0
+            launches = B.tr_launch_count() - launches0
         if world > 1:
             torch.distributed.barrier()
         B.tr_check(ex)
@@ -835,7 +837,10 @@ def main():
         traffic = traffic * h["n"] / traffic_n
     line = {
         "metric": METRIC, "value": world * h["n"] / (ms_step * 1e-3), "unit": "elements/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "step_ms": {"min": round(min(h["per_ms"]), 5), "median": round(statistics.median(h["per_ms"]), 5),
+                    "max": round(max(h["per_ms"]), 5)},
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": h["n"], "n_seg": h["nseg"], "map": "rational 6/6",
                    "l2": "inputs (1 GiB) larger than L2 (126 MB); no flush", "parallelism": f"replicas x{world}"},
