@@ -84,6 +84,54 @@ def test_map_float(orc, B, mi, dt, n, off):
     assert np.array_equal(got.view(np.int64), orc.map_values_f32(oracle_map(orc, m), xh).view(np.int64))
 
 
+def _newton_magnitude_mix(seed: int) -> np.ndarray:
+    """Groups of four consecutive f32 values (one 16-byte vector, the map
+    kernel's unit): groups wholly inside [2^-60, 2^28] in magnitude (the Newton
+    map's guard-free steps), groups on and just inside those edges, and groups
+    holding one value outside them (zeros, subnormals, tiny, huge, infinities,
+    NaN, and the edges' outer neighbours), which take the guarded steps."""
+    g = np.random.default_rng(seed)
+    f32 = np.float32
+
+    def signed(mag):
+        return (mag * np.where(g.random(mag.size) < 0.5, -1.0, 1.0)).astype(f32)
+
+    inside = signed(np.exp2(g.uniform(-60, 28, 4 * 20000)))
+    lo, hi = f32(2.0 ** -60), f32(2.0 ** 28)
+    edge_in = np.array([lo, hi, np.nextafter(lo, f32(1)), np.nextafter(hi, f32(0))], f32)
+    edges = signed(np.resize(edge_in, 4 * 500).astype(np.float64))
+    outer = np.array([0.0, -0.0, 1e-45, -1e-45, 1.17549435e-38, 2.0 ** -100, 2.0 ** 40, 3.4028235e38, np.inf,
+                      -np.inf, np.nan, np.nextafter(lo, f32(0)), np.nextafter(hi, f32(np.inf)), 2.0 ** -61],
+                     f32)
+    mixed = signed(np.exp2(g.uniform(-60, 28, 4 * 3000))).reshape(-1, 4)
+    mixed[np.arange(mixed.shape[0]), g.integers(0, 4, mixed.shape[0])] = g.choice(outer, mixed.shape[0])
+    wide = signed(np.exp2(g.uniform(-149, 127, 4 * 5000)))
+    groups = np.concatenate([inside.reshape(-1, 4), edges.reshape(-1, 4), mixed, wide.reshape(-1, 4)])
+    return groups[g.permutation(groups.shape[0])].ravel()
+
+
+@pytest.mark.parametrize("iters", [6, 40])
+def test_newton_all_magnitudes_bitexact(orc, B, iters):
+    """The Newton cube root runs without its guards when every value of a
+    vector lies in [2^-60, 2^28] in magnitude: over values of every magnitude,
+    the edges and the special values, the map equals the oracle's binary32
+    evaluation bit for bit (NaN as NaN), and a reduction over the guard-free
+    values gives the oracle's minimum and maximum exactly."""
+    m = I.newton_map(iters)
+    xh = _newton_magnitude_mix(500 + iters)
+    y = torch.empty(xh.size, dtype=torch.float32, device="cuda")
+    B.tr_map(m, torch.from_numpy(xh).cuda(), y)
+    got = y.cpu().numpy()
+    ref = orc.map_values_f32(oracle_map(orc, m), xh.astype(np.float64)).astype(np.float32)
+    same = (got.view(np.int32) == ref.view(np.int32)) | (np.isnan(got) & np.isnan(ref))
+    assert np.all(same), (xh[~same][:8], got[~same][:8], ref[~same][:8])
+    fin = xh[(np.abs(xh) >= 2.0 ** -60) & (np.abs(xh) <= 2.0 ** 28)]
+    s, lo, hi = reduce_dev(B, m, torch.from_numpy(fin).cuda())
+    f = orc.map_values_f32(oracle_map(orc, m), fin.astype(np.float64))
+    assert lo == np.min(f) and hi == np.max(f)
+    assert abs(s - np.sum(f.astype(np.float64))) <= 1e-6 * np.sum(np.abs(f))
+
+
 @pytest.mark.parametrize("deg", [0, 1, 3, 5, 13, 16, 17, 24])
 def test_horner_runtime_degrees(orc, B, deg):
     """Horner maps of run-time degree (packed up to degree 16, the coefficient
