@@ -132,6 +132,42 @@ def test_newton_all_magnitudes_bitexact(orc, B, iters):
     assert abs(s - np.sum(f.astype(np.float64))) <= 1e-6 * np.sum(np.abs(f))
 
 
+def test_rational_all_magnitudes_bitexact(orc, B):
+    """The rational map over inputs of every magnitude (groups of four inside
+    [-512, 512], groups far outside it, values next to the numerator's real
+    roots, and the special values): the division-free quotient where the
+    guard admits it, the IEEE division elsewhere, and the map equals the
+    oracle's binary32 evaluation bit for bit."""
+    g = np.random.default_rng(2309)
+    cp = I.f32_exact(g.standard_normal(7))
+    m = I.rational_map(cp, I.f32_exact(I.positive_even_q(g, 6)))
+    f32 = np.float32
+    inside = g.uniform(-512, 512, 4 * 20000)
+    roots = np.roots(np.asarray(cp, np.float64)[::-1])
+    roots = roots[np.abs(roots.imag) < 1e-12].real
+    near = np.concatenate([[np.nextafter(f32(r), f32(d * np.inf)) for d in (-1, 1) for _ in range(2)] for r in roots]
+                          + [np.zeros(0)])
+    outside = g.choice([-1.0, 1.0], 4 * 5000) * np.exp2(g.uniform(-149, 127, 4 * 5000))
+    special = np.array([0.0, -0.0, 1e-45, np.inf, -np.inf, np.nan, 512.0, -512.0, 512.00006, 3.4028235e38], f32)
+    groups = [inside.astype(f32).reshape(-1, 4), outside.astype(f32).reshape(-1, 4),
+              np.resize(np.concatenate([near, special]).astype(f32), 4 * 200).reshape(-1, 4)]
+    mixed = g.uniform(-2, 2, 4 * 2000).astype(f32).reshape(-1, 4)
+    mixed[:, 0] = g.choice(np.concatenate([special, near.astype(f32)]), mixed.shape[0])
+    groups.append(mixed)
+    x = np.concatenate(groups)
+    x = x[g.permutation(x.shape[0])].ravel()
+    y = torch.empty(x.size, dtype=torch.float32, device="cuda")
+    B.tr_map(m, torch.from_numpy(x).cuda(), y)
+    got = y.cpu().numpy()
+    ref = orc.map_values_f32(oracle_map(orc, m), x.astype(np.float64)).astype(np.float32)
+    same = (got.view(np.int32) == ref.view(np.int32)) | (np.isnan(got) & np.isnan(ref))
+    assert np.all(same), (x[~same][:8], got[~same][:8], ref[~same][:8])
+    # the reduce kernel's 16-value groups on the same values: min / max exact
+    s, lo, hi = reduce_dev(B, m, torch.from_numpy(x[np.isfinite(x) & (np.abs(x) <= 512)]).cuda())
+    f = orc.map_values_f32(oracle_map(orc, m), x[np.isfinite(x) & (np.abs(x) <= 512)].astype(np.float64))
+    assert lo == np.min(f) and hi == np.max(f)
+
+
 @pytest.mark.parametrize("deg", [0, 1, 3, 5, 13, 16, 17, 24])
 def test_horner_runtime_degrees(orc, B, deg):
     """Horner maps of run-time degree (packed up to degree 16, the coefficient
